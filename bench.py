@@ -1,0 +1,440 @@
+#!/usr/bin/env python3
+"""Benchmark of the AMR dual-mesh + iso-surface hot path on one B300.
+
+One step = the whole path over one data set resident in HBM:
+  amr_upload (device arrays) -> amr_build_locator -> amr_dual_cells -> amr_iso
+Prints one JSON line (rank 0). `value` = dual cells per second of step time;
+triangles/s, per-stage rates, the dominant kernel's roofline (live CUDA
+events, algorithmic bytes / launch time / measured HBM copy peak), an
+end-to-end figure through the C ABI with host buffers, SM clocks sampled
+during the timed region and the CPU oracle timed on a bounded sample are
+added to the same line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload wing|octree|block|sphere]
+  python bench.py --impl reference ...   (the CPU oracle as the reference arm)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_08475_b300 import synth  # noqa: E402
+
+METRIC = "dual cells/s + triangles/s (1 B300, % HBM roofline); served p50/p99 latency"
+
+WORKLOADS = {
+    "wing": ("wing_bands: Exajet-sized AMR, widths 1-8 in distance bands around a swept wing, "
+             "holes in the solid, log-normal scalar (sigma 2)", lambda dev: synth.wing_bands(device=dev)),
+    "octree": ("octree_gaussians: 512^3 octree AMR, widths 1-16, |grad f| w refinement, "
+               "iso = 60th percentile", lambda dev: synth.octree_gaussians(device=dev)),
+    "block": ("block_vortex: 8^3-cell blocks, widths 1-8, 4096x2048x2048, 5% holes, |curl| of "
+              "vortex rings", lambda dev: synth.block_vortex(device=dev)),
+    "sphere": ("sphere_tiny: 32^3, 2 levels, distance field, iso 8", lambda dev: synth.sphere_tiny(device=dev)),
+}
+
+
+def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int) -> float:
+    """Compulsory bytes per launch of each kernel under the library's data
+    layout: what the kernel must read and write at least once."""
+    return {
+        "k_insert_bricks": 17.0 * n,                 # xyz + level + scalar
+        "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
+        "k_resolve_views": 8.0 * n_slots,            # read id, write view
+        "k_dual_cells": 4.0 * n_slots + 32.0 * nd,   # read views once, write 8 slots / dual
+        "k_mc": 32.0 * nd + 4.0 * n + 36.0 * nt,     # read tuples + scalars, write triangles
+    }.get(kernel, 0.0)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2004_08475_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str, units: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled by units
+    processed; None when absent or taken on another version of the kernels."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{kernel}:{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_unit"]) * units
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (bounded sample)
+# ---------------------------------------------------------------------------
+
+def oracle_window(xyz, lv, s, target_cells: int, seed: int = 0):
+    """Cells inside a box around a finest-level cell holding about
+    `target_cells` cells (numpy arrays in, numpy arrays out)."""
+    x = xyz.astype(np.int64)
+    lo, hi = x.min(0), x.max(0) + 1
+    fine = np.where(lv == lv.min())[0]
+    rng = np.random.default_rng(seed)
+    c = x[fine[rng.integers(0, fine.shape[0])]] if fine.size else (lo + hi) // 2
+    frac = min(1.0, target_cells / max(1, x.shape[0]))
+    half = np.maximum((hi - lo) * frac ** (1 / 3) / 2, 1)
+    m = np.ones(x.shape[0], dtype=bool)
+    for _ in range(40):
+        m = (np.abs(x - c) <= half).all(1)
+        k = int(m.sum())
+        if 0.8 * target_cells <= k <= 1.25 * target_cells or k == x.shape[0]:
+            break
+        half = half * (target_cells / max(k, 1)) ** (1 / 3)
+    return xyz[m], lv[m], s[m]
+
+
+def time_oracle(xyz, lv, s, iso, seconds: float = 15.0):
+    """Oracle (cell set + duals + MC) on a window sized for about `seconds`
+    of single-thread CPU work; returns counts and the time taken."""
+    import oracle
+    target = 20000
+    while True:
+        wx, wl, ws = oracle_window(xyz, lv, s, target)
+        t0 = time.perf_counter()
+        m = oracle.OracleMesh(wx, wl)
+        d = m.duals()
+        r = m.iso(ws, d, iso, want_keys=False)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or target > 2e7 or target >= xyz.shape[0]:
+            break
+        target = int(target * min(8.0, seconds / max(dt, 1e-3)))
+    return {"duals": int(d.shape[0]), "tris": int(r["tris"].shape[0]), "cells": int(wx.shape[0]),
+            "seconds": dt}
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args, workload_desc, gen):
+    """Reference arm: the CPU oracle as it stands, on this run's workload
+    (bounded samples), rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dev = "cuda" if (torch.cuda.is_available() and args.workload in ("wing", "block")) else "cpu"
+    xyz, lv, s, iso, info = gen(dev)
+    x, l, v = xyz.cpu().numpy(), lv.cpu().numpy(), s.cpu().numpy()
+    per = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        time_oracle(x, l, v, iso, seconds=per)
+    duals = tris = 0
+    secs = 0.0
+    cells = 0
+    for _ in range(args.steps):
+        r = time_oracle(x, l, v, iso, seconds=per)
+        duals += r["duals"]
+        tris += r["tris"]
+        secs += r["seconds"]
+        cells = r["cells"]
+    value = duals / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "dual cells/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": workload_desc, "n_cells": info["n"],
+                   "sample_cells": cells},
+        "triangles_per_s": tris / secs,
+        "cpu_baseline": {"value": value, "unit": "dual cells/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{cells} cells in a box of the {args.workload} workload per step"},
+        "e2e": {"value": value, "unit": "dual cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="wing", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2-brick", type=int, default=3)
+    ap.add_argument("--load-factor", type=float, default=0.5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--batch-isos", type=int, default=16)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    desc, gen = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        run_reference(args, desc, gen)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2004_08475_b300 import amriso
+
+    xyz, lv, s, iso, info = gen("cuda")
+    n = info["n"]
+    stream = torch.cuda.current_stream()
+    ctx = amriso.AmrContext(local, stream)
+    opts = dict(log2_brick=args.log2_brick, load_factor=args.load_factor)
+
+    def step(tri_buf):
+        ctx.upload(xyz, lv, s)
+        ctx.build_locator(**opts)
+        nd = ctx.dual_cells()
+        nt = ctx.iso_count(iso, tri_buf)
+        return nd, nt
+
+    # size the triangle buffer once (exact count), then warm up
+    ctx.upload(xyz, lv, s)
+    ctx.build_locator(**opts)
+    ctx.dual_cells()
+    nt0 = ctx.iso_count(iso, torch.empty((1, 3, 3), dtype=torch.float32, device="cuda"))
+    tri_buf = torch.empty((max(nt0, 1), 3, 3), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step(tri_buf)
+    torch.cuda.synchronize()
+    ctx.kernel_times()          # discard warm-up timings
+    ctx.enable_timing(True)
+
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            nd, nt = step(tri_buf)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(stop) / args.steps
+    ktimes = ctx.kernel_times()
+    ctx.enable_timing(False)
+    inf = ctx.info()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([float(nd), float(nt)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tot)
+        nd_all, nt_all = tot.tolist()
+    else:
+        nd_all, nt_all = float(nd), float(nt)
+
+    kt = {k: v for k, v in ktimes.items() if v[1] > 0}
+    t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_resolve_views")) / args.steps
+    t_dual = kt.get("k_dual_cells", (0, 1))[0] / args.steps
+    t_iso = kt.get("k_mc", (0, 1))[0] / args.steps
+    launches = int(sum(v[1] for v in kt.values()))
+
+    # roofline of the dominant kernel
+    peak, peak_src = load_peaks()
+    total_kms = max(1e-9, sum(v[0] for v in kt.values()))
+    kernels = {}
+    for k, (tot_ms, cnt) in kt.items():
+        per = tot_ms / cnt
+        b = algorithmic_bytes(k, n, inf.n_slots, nd, nt)
+        kernels[k] = {"ms_per_launch": per, "launches": cnt, "share": tot_ms / total_kms,
+                      "algorithmic_bytes": b, "gbs": b / per / 1e6 if per > 0 else 0.0}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
+    dk = kernels[dom]
+    units = {"k_insert_bricks": n, "k_scatter_cells": n, "k_resolve_views": inf.n_slots,
+             "k_dual_cells": inf.n_slots, "k_mc": nd}.get(dom, n)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dk["gbs"] / peak, "peak_source": peak_src,
+                "traffic": ncu_traffic(dom, args.workload, units),
+                "algorithmic_bytes_per_launch": dk["algorithmic_bytes"]}
+    step_bytes = sum(algorithmic_bytes(k, n, inf.n_slots, nd, nt) * v[1] / args.steps for k, v in kt.items())
+
+    # batched multi-iso over the resident dual cells
+    batch = None
+    if args.batch_isos > 0 and rank == 0:
+        srt = torch.sort(s).values
+        lo_q, hi_q = 0.40, 0.95
+        isos = [float(srt[int((lo_q + (hi_q - lo_q) * k / max(1, args.batch_isos - 1)) * (n - 1))])
+                for k in range(args.batch_isos)]
+        del srt
+        _, offs = ctx.iso_batch(isos, torch.empty((0, 3, 3), dtype=torch.float32, device="cuda"))
+        need = int(offs[-1])
+        torch.cuda.empty_cache()
+        buf = torch.empty((max(need, 1), 3, 3), dtype=torch.float32, device="cuda")
+        ctx.iso_batch(isos, buf)
+        torch.cuda.synchronize()
+        ctx.kernel_times()
+        ctx.enable_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.iso_batch(isos, buf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bt = ctx.kernel_times()
+        ctx.enable_timing(False)
+        bms = e0.elapsed_time(e1) / reps
+        batch = {"n_iso": len(isos), "iso_quantiles": [lo_q, hi_q], "ms": bms, "triangles": need,
+                 "triangles_per_s": need / (bms / 1e3), "ms_per_iso": bms / len(isos),
+                 "single_iso_kernel_ms": t_iso,
+                 "kernels_ms": {k: v[0] / reps for k, v in bt.items() if v[1]}}
+        del buf
+        torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hx, hl, hs = xyz.cpu().pin_memory(), lv.cpu().pin_memory(), s.cpu().pin_memory()
+        hout = torch.empty((max(nt, 1), 3, 3), dtype=torch.float32).pin_memory()
+        ectx = amriso.AmrContext(local, stream)
+
+        def e2e_step():
+            ectx.upload(hx, hl, hs)
+            ectx.build_locator(**opts)
+            d = ectx.dual_cells()
+            t = ectx.iso_count(iso, hout)
+            return d, t
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            d2, t2 = e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        assert d2 == nd and t2 == nt
+        e2e = {"value": nd_all / e2e_s, "unit": "dual cells/s", "h2d_bytes_per_step": int(17 * n),
+               "d2h_bytes_per_step": int(36 * nt), "ms_per_step": 1000.0 * e2e_s,
+               "triangles_per_s": nt_all / e2e_s}
+        ectx.close()
+        del hx, hl, hs, hout
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        x, l, v = xyz.cpu().numpy(), lv.cpu().numpy(), s.cpu().numpy()
+        r = time_oracle(x, l, v, iso, seconds=15.0)
+        cpu = {"value": r["duals"] / r["seconds"], "unit": "dual cells/s", "cores": 1, "kind": "oracle",
+               "sample": f"{r['cells']} cells in a box of the {args.workload} workload "
+                         f"({r['duals']} duals, {r['tris']} triangles, {r['seconds']:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": nd_all / (ms / 1e3),
+            "unit": "dual cells/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n_cells": n,
+                       "n_dual": nd, "n_triangles": nt, "iso": iso, "n_bricks": inf.n_bricks,
+                       "n_slots": inf.n_slots, "levels": inf.n_levels, "log2_brick": args.log2_brick,
+                       "load_factor": args.load_factor, "parallelism": f"replicas{world}",
+                       "l2": f"inputs larger than L2 ({(17 * n) / 1e6:.0f} MB of cells)"},
+            "triangles_per_s": nt_all / (ms / 1e3),
+            "rates": {"dual_cells_per_s_locator_plus_dual": nd / ((t_loc + t_dual) / 1e3) if t_loc + t_dual else None,
+                      "triangles_per_s_iso_kernel": nt / (t_iso / 1e3) if t_iso else None,
+                      "step_algorithmic_gbs": step_bytes / (ms / 1e3) / 1e9,
+                      "step_frac_of_peak": step_bytes / (ms / 1e3) / 1e9 / peak},
+            "roofline": roofline,
+            "kernels": kernels,
+            "batched_iso": batch,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "gpu": torch.cuda.get_device_name(local),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

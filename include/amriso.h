@@ -1,0 +1,190 @@
+/*
+ * amriso.h - C ABI of the B300 (sm_103a) library for dual meshes and
+ * crack-free iso-surfaces of AMR data, after Wald, "A Simple, General, and
+ * GPU Friendly Method for Computing Dual Mesh and Iso-Surfaces of AMR Data".
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: AMR_OK (0) or a negative AMR_ERR_* code. No C++ exception
+ *     crosses this boundary. Out-parameters are written only on AMR_OK,
+ *     except where an entry point says otherwise.
+ *   - A cell is its lower corner (i, j, k) in finest-level units (int32) and
+ *     its level l (uint8; level 0 is finest, width 2^l); the corner must be a
+ *     multiple of 2^l (Sec. 3.1). Cell ID = the cell's index in the arrays
+ *     given to amr_upload.
+ *   - All device work runs on the context's CUDA stream, in call order.
+ *     Entry points that return a count synchronise that stream once.
+ *   - Pointers are device pointers unless the call's `flags` contains
+ *     AMR_HOST_PTRS, in which case the library copies between host and
+ *     device itself (inside the call).
+ *   - One context holds one data set and everything derived from it. A
+ *     context may be used from one host thread at a time.
+ */
+#ifndef AMRISO_H
+#define AMRISO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define AMR_OK                0
+#define AMR_ERR_INVALID_ARG  (-1)  /* null pointer, negative size, bad option */
+#define AMR_ERR_UNALIGNED    (-2)  /* a lower corner is not a multiple of 2^l */
+#define AMR_ERR_RANGE        (-3)  /* level > 14, extent >= 2^21 units per axis,
+                                      a coordinate beyond +-2^30, or more than
+                                      2^31-1 cells / brick slots */
+#define AMR_ERR_NONFINITE    (-4)  /* a scalar is NaN or infinite */
+#define AMR_ERR_DUPLICATE    (-5)  /* two cells with the same (i,j,k;l) */
+#define AMR_ERR_OVERLAP      (-6)  /* a cell lies inside a coarser cell */
+#define AMR_ERR_STATE        (-7)  /* call out of order (e.g. amr_iso before
+                                      amr_dual_cells) */
+#define AMR_ERR_OOM          (-8)  /* device allocation failed */
+#define AMR_ERR_CAPACITY     (-9)  /* output buffer too small; the exact
+                                      required count is still reported */
+#define AMR_ERR_TIMEOUT      (-10) /* a bounded device wait ran out */
+#define AMR_ERR_CUDA         (-11) /* any other CUDA runtime error */
+
+/* ---- flags --------------------------------------------------------------- */
+#define AMR_DEVICE_PTRS 0  /* arrays are device memory */
+#define AMR_HOST_PTRS   1  /* arrays are host memory (pageable or pinned) */
+#define AMR_COPY        2  /* amr_upload only: copy device arrays instead of
+                              borrowing them */
+
+typedef struct amr_ctx amr_ctx;
+
+/* Options of the point-location structure (Sec. 3.2). A zeroed struct or a
+ * NULL pointer selects the defaults given in brackets. */
+typedef struct amr_locator_opts {
+  int   log2_brick;     /* brick edge 2^log2_brick cells: 2 or 3          [3] */
+  float load_factor;    /* target fill of the brick hash table, 0.05-0.9 [0.5] */
+  int   block_size;     /* threads per block of cell-parallel kernels   [256] */
+  int   check_overlap;  /* nonzero: reject cells inside coarser cells     [0] */
+} amr_locator_opts;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device`, working on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). */
+int amr_create(amr_ctx** out, int device, void* cuda_stream);
+
+/* Releases the context and every device buffer it owns. NULL is ignored. */
+void amr_destroy(amr_ctx* ctx);
+
+/* Replaces the context's stream (subsequent calls run on it). */
+int amr_set_stream(amr_ctx* ctx, void* cuda_stream);
+
+/* ---- the hot path (Sec. 3-5) -------------------------------------------- */
+
+/* Input of the method: the unordered list of actual cells and one fp32
+ * scalar per cell (Sec. 3.1; the thrust driver of Sec. 5.2 uploads the same
+ * list).
+ *   xyz    [n][3] int32 lower corners, finest-level units
+ *   level  [n]    uint8 levels
+ *   scalar [n]    fp32 cell-centred values
+ * With AMR_HOST_PTRS the arrays are copied to the device inside the call.
+ * With device pointers the arrays are borrowed: they must stay valid and
+ * unchanged until amr_build_locator returns (AMR_COPY copies them instead).
+ * Validation (alignment, level range, finiteness) happens in
+ * amr_build_locator. Invalidates any locator / dual cells of the context. */
+int amr_upload(amr_ctx* ctx, const int32_t* xyz, const uint8_t* level,
+               const float* scalar, int64_t n, int flags);
+
+/* Builds the cell-location structure behind snap() (Sec. 3.2): per-level
+ * bricks of 2^log2_brick cells per axis in one open-addressing hash table,
+ * with every brick slot resolved to the actual cell that contains it (the
+ * slot's own cell, a coarser cell, or none). Validates the input and fails
+ * with AMR_ERR_UNALIGNED / RANGE / NONFINITE / DUPLICATE (and OVERLAP when
+ * requested). Synchronises the stream. */
+int amr_build_locator(amr_ctx* ctx, const amr_locator_opts* opts);
+
+/* Emits every dual cell exactly once (Sec. 4.2-4.4): for every actual cell
+ * its 8 logical duals, snapped, and kept unless a vertex is missing (rule 1),
+ * finer (rule 2) or a same-level vertex is lower than the cell (rule 3). The
+ * dual list stays resident in the context for later amr_iso calls.
+ * *n_dual receives the number of dual cells. Synchronises the stream. */
+int amr_dual_cells(amr_ctx* ctx, int64_t* n_dual);
+
+/* Copies the resident dual cells as cell IDs: out[n_dual][8] int32, vertex
+ * order e = ex + 2 ey + 4 ez (vertex e sits at the logical cell offset e
+ * from the dual's lowest vertex). The order of the dual cells is unspecified
+ * but equals the order of amr_iso_cases' outputs. cap = rows of `out`;
+ * AMR_ERR_CAPACITY when cap < n_dual (nothing written). */
+int amr_get_duals(amr_ctx* ctx, int32_t* out, int64_t cap, int flags);
+
+/* Marching Cubes on every resident dual cell, degenerate or not (Sec. 5):
+ * case bit e set iff s(vertex e) > iso; on each crossed edge the vertex is
+ * interpolated between the two cell centres (from the endpoint with the
+ * lower (z,y,x) corner, fp32, t = (iso - sa) / (sb - sa), P = ca + t (cb - ca),
+ * no fused multiply-add); triangles without three different vertices (edge
+ * keys) are dropped (Sec. 5); survivors are appended through a counter with
+ * a capacity check (Sec. 5.2).
+ *   tris [cap][3][3] fp32 "fat" triangles (3 complete vertices each),
+ *        normals (right-hand rule) point toward decreasing s.
+ *   *n_tris receives the exact triangle count; it is also written with
+ *        AMR_ERR_CAPACITY when the count exceeds cap (then only the first
+ *        cap triangles, in unspecified order, were written).
+ * Synchronises the stream. */
+int amr_iso(amr_ctx* ctx, float iso, float* tris, int64_t cap, int64_t* n_tris,
+            int flags);
+
+/* Per-dual MC case index and number of kept triangles at `iso`, in the order
+ * of amr_get_duals: cases[n_dual] uint8, ntri[n_dual] uint8 (either may be
+ * NULL). Synchronises the stream. */
+int amr_iso_cases(amr_ctx* ctx, float iso, uint8_t* cases, uint8_t* ntri,
+                  int flags);
+
+/* Several iso-values over the resident dual cells in one persistent launch:
+ * each dual's vertex IDs and scalars are read once for all values.
+ *   isos    [n_iso] host array, 1 <= n_iso <= 64
+ *   tris    [cap][3][3] device (or host, AMR_HOST_PTRS) output; iso k's
+ *           triangles occupy rows offsets[k] .. offsets[k+1]-1
+ *   offsets [n_iso+1] host int64, written on AMR_OK and on AMR_ERR_CAPACITY
+ *           (then offsets[n_iso] is the required cap and nothing was
+ *           written).
+ * Synchronises the stream. */
+int amr_iso_batch(amr_ctx* ctx, const float* isos, int n_iso, float* tris,
+                  int64_t cap, int64_t* offsets, int flags);
+
+/* Waits for all work queued on the context's stream. */
+int amr_sync(amr_ctx* ctx);
+
+/* Human-readable text for a return code (static storage). */
+const char* amr_strerror(int code);
+
+/* ---- introspection (host only, no device needed) ------------------------ */
+
+/* The Marching Cubes triangle table the kernels use (Sec. 5.1; generated by
+ * the library from its face rule, not copied from any other table):
+ *   count[256]      triangles per case (0..5)
+ *   edges[256][15]  edge indices, 3 per triangle, unused entries 255.
+ * Edge k joins hexahedron corners (a,b), a < b, listed in increasing (a,b)
+ * order; corner e sits at (e & 1, (e >> 1) & 1, e >> 2). */
+int amr_mc_table(uint8_t* count, uint8_t* edges);
+
+/* Sizes of the context's resident state. */
+typedef struct amr_info {
+  int64_t n_cells;
+  int64_t n_bricks;
+  int64_t n_slots;      /* n_bricks * 2^(3 log2_brick) */
+  int64_t n_dual;       /* -1 before amr_dual_cells */
+  int32_t n_levels;     /* max level + 1 */
+  int32_t log2_brick;
+  int64_t device_bytes; /* device memory held by the context */
+} amr_info;
+int amr_get_info(amr_ctx* ctx, amr_info* info);
+
+/* Per-kernel device time (CUDA events on the context's stream) accumulated
+ * since the last call, for the kernels listed by amr_kernel_name(0..n-1).
+ * Timing is off until amr_enable_timing(ctx, 1). ms[] receives one value per
+ * kernel, launches[] the number of launches (either may be NULL). Returns the
+ * number of kernels. Synchronises the stream. */
+int amr_enable_timing(amr_ctx* ctx, int on);
+int amr_kernel_times(amr_ctx* ctx, double* ms, int64_t* launches, int n);
+const char* amr_kernel_name(int k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMRISO_H */

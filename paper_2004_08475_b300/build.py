@@ -1,0 +1,51 @@
+"""Builds libamriso.so in-tree with nvcc for sm_103a (B300)."""
+from __future__ import annotations
+
+import glob
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(HERE, "libamriso.so")
+SOURCES = ["kernels.cu", "api.cu", "mc_table.cpp"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _inputs():
+    files = [os.path.join(CSRC, s) for s in SOURCES]
+    files += glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return files
+
+
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(f) <= t for f in _inputs())
+
+
+def nvcc_command(out: str, ptxas_verbose: bool = False):
+    cmd = ["nvcc", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+           "-I", INCLUDE, "-I", CSRC, "-o", out]
+    if ptxas_verbose:
+        cmd += ["-Xptxas", "-v"]
+    return cmd + [os.path.join(CSRC, s) for s in SOURCES]
+
+
+def build(force: bool = False, ptxas_verbose: bool = False) -> str:
+    """Compile the CUDA library (no GPU needed: nvcc cross-compiles)."""
+    if not force and up_to_date():
+        return LIB
+    tmp = LIB + ".tmp"
+    subprocess.check_call(nvcc_command(tmp, ptxas_verbose))
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, ptxas_verbose="-v" in sys.argv)
+    print(LIB)

@@ -1,0 +1,631 @@
+// C ABI of libamriso (declared in include/amriso.h): contexts, device memory,
+// stream-ordered launch sequences and error mapping around the kernels.
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "amriso.h"
+#include "kernels.h"
+#include "mc_table.h"
+
+using namespace amriso;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+enum KernelId {
+  KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
+  KT_GET_DUALS, KT_COUNT
+};
+const char* const kKernelNames[KT_COUNT] = {
+    "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
+    "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals"};
+
+const McTable& host_table() {
+  static McTable t = [] {
+    McTable x;
+    make_mc_table(&x);
+    return x;
+  }();
+  return t;
+}
+
+McConst make_mc_const() {
+  const McTable& t = host_table();
+  McConst m;
+  for (int c = 0; c < 256; ++c) {
+    m.packed[c] = t.packed[c];
+    m.count[c] = t.count[c];
+  }
+  m.edge_a = 0;
+  m.edge_b = 0;
+  for (int k = 0; k < 12; ++k) {
+    m.edge_a |= (unsigned long long)t.edge_a[k] << (4 * k);
+    m.edge_b |= (unsigned long long)t.edge_b[k] << (4 * k);
+  }
+  return m;
+}
+
+}  // namespace
+
+struct amr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 148;
+  // input (borrowed or owned)
+  long long n = 0;
+  const int* xyz = nullptr;
+  const unsigned char* lvl = nullptr;
+  const float* s = nullptr;
+  DevBuf own_xyz, own_lvl, own_s;
+  int stage = 0;  // 0 empty, 1 uploaded, 2 locator, 3 dual cells
+  // locator
+  int logb = 3;
+  float alpha = 0.5f;
+  int block = 256;
+  int check_overlap = 0;
+  DevBuf hkeys, hvals, bricks, cell_id, scal, view;
+  unsigned long long hcap = 0;
+  long long n_bricks = 0, n_slots = 0;
+  int levels = 0;
+  // dual cells
+  DevBuf duals;
+  long long dual_cap = 0, n_dual = -1;
+  // scratch
+  DevBuf scratch;
+  Scratch* host_sc = nullptr;  // pinned mirror
+  DevBuf stage_buf, iso_buf, seg_buf;
+  McConst mc;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[KT_COUNT];
+  double ms_acc[KT_COUNT] = {0};
+  long long launches[KT_COUNT] = {0};
+};
+
+namespace {
+
+size_t held(const DevBuf& b) { return b.bytes; }
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (b.bytes >= bytes) return AMR_OK;
+  release(b);
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return AMR_ERR_OOM;
+  }
+  b.bytes = bytes;
+  return AMR_OK;
+}
+
+int cuda_rc(cudaError_t e) {
+  if (e == cudaSuccess) return AMR_OK;
+  if (e == cudaErrorMemoryAllocation) return AMR_ERR_OOM;
+  return AMR_ERR_CUDA;
+}
+
+#define AMR_TRY(x)                 \
+  do {                             \
+    const int rc_ = (x);           \
+    if (rc_ != AMR_OK) return rc_; \
+  } while (0)
+
+#define AMR_CUDA(x) AMR_TRY(cuda_rc(x))
+
+cudaEvent_t take_event(amr_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records an event pair around one kernel launch when timing is on.
+struct KernelTimer {
+  amr_ctx* c;
+  int k;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KernelTimer(amr_ctx* c_, int k_) : c(c_), k(k_) {
+    if (c->timing) {
+      a = take_event(c);
+      b = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~KernelTimer() {
+    if (c->timing) {
+      cudaEventRecord(b, c->stream);
+      c->pending[k].push_back({a, b});
+      c->launches[k]++;
+    }
+  }
+};
+
+Scratch* dev_sc(amr_ctx* c) { return static_cast<Scratch*>(c->scratch.p); }
+
+// Resets the device scratch counters (stream-ordered).
+int reset_scratch(amr_ctx* c) {
+  Scratch& h = *c->host_sc;
+  std::memset(&h, 0, sizeof(Scratch));
+  for (int a = 0; a < 3; ++a) {
+    h.lo[a] = INT_MAX;
+    h.hi[a] = INT_MIN;
+  }
+  AMR_CUDA(cudaMemcpyAsync(dev_sc(c), &h, sizeof(Scratch), cudaMemcpyHostToDevice, c->stream));
+  return AMR_OK;
+}
+
+int read_scratch(amr_ctx* c) {
+  AMR_CUDA(cudaMemcpyAsync(c->host_sc, dev_sc(c), sizeof(Scratch), cudaMemcpyDeviceToHost, c->stream));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return AMR_OK;
+}
+
+int err_code(unsigned e) {
+  if (e & ERR_NONFINITE) return AMR_ERR_NONFINITE;
+  if (e & ERR_RANGE) return AMR_ERR_RANGE;
+  if (e & ERR_UNALIGNED) return AMR_ERR_UNALIGNED;
+  if (e & ERR_DUPLICATE) return AMR_ERR_DUPLICATE;
+  if (e & ERR_OVERLAP) return AMR_ERR_OVERLAP;
+  if (e & ERR_TIMEOUT) return AMR_ERR_TIMEOUT;
+  if (e & ERR_HASH_FULL) return AMR_ERR_CAPACITY;
+  return AMR_OK;
+}
+
+Locator make_locator(amr_ctx* c) {
+  Locator L;
+  L.hkeys = static_cast<const unsigned long long*>(c->hkeys.p);
+  L.hvals = static_cast<const int*>(c->hvals.p);
+  L.hmask = c->hcap - 1;
+  L.bricks = static_cast<const int4*>(c->bricks.p);
+  L.cell_id = static_cast<const int*>(c->cell_id.p);
+  L.scal = static_cast<const float*>(c->scal.p);
+  L.view = static_cast<const unsigned*>(c->view.p);
+  L.levels = c->levels;
+  return L;
+}
+
+int grid_for(amr_ctx* c, long long items, int block, int per_sm) {
+  const long long want = (items + block - 1) / block;
+  const long long cap = (long long)c->sm_count * per_sm;
+  return (int)std::max(1ll, std::min(want, cap));
+}
+
+unsigned long long pow2_at_least(unsigned long long v) {
+  unsigned long long p = 1024;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Copies `bytes` from device `src` to `dst` (device or host per flags).
+int deliver(amr_ctx* c, void* dst, const void* src, size_t bytes, int flags) {
+  if (bytes == 0 || dst == src) return AMR_OK;
+  const cudaMemcpyKind kind = (flags & AMR_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  AMR_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+  return AMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* amr_strerror(int code) {
+  switch (code) {
+    case AMR_OK: return "ok";
+    case AMR_ERR_INVALID_ARG: return "invalid argument";
+    case AMR_ERR_UNALIGNED: return "lower corner not a multiple of the cell width";
+    case AMR_ERR_RANGE: return "level, extent or size out of range";
+    case AMR_ERR_NONFINITE: return "non-finite scalar";
+    case AMR_ERR_DUPLICATE: return "duplicate cell";
+    case AMR_ERR_OVERLAP: return "cell inside a coarser cell";
+    case AMR_ERR_STATE: return "call out of order";
+    case AMR_ERR_OOM: return "device out of memory";
+    case AMR_ERR_CAPACITY: return "output capacity exceeded";
+    case AMR_ERR_TIMEOUT: return "bounded device wait timed out";
+    case AMR_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown error";
+  }
+}
+
+int amr_mc_table(uint8_t* count, uint8_t* edges) {
+  if (!count && !edges) return AMR_ERR_INVALID_ARG;
+  const McTable& t = host_table();
+  if (count) std::memcpy(count, t.count, 256);
+  if (edges) std::memcpy(edges, t.edges, 256 * 15);
+  return AMR_OK;
+}
+
+int amr_create(amr_ctx** out, int device, void* cuda_stream) {
+  if (!out) return AMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return AMR_ERR_INVALID_ARG;
+  }
+  AMR_CUDA(cudaSetDevice(device));
+  amr_ctx* c = new (std::nothrow) amr_ctx();
+  if (!c) return AMR_ERR_OOM;
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost(reinterpret_cast<void**>(&c->host_sc), sizeof(Scratch)) != cudaSuccess ||
+      ensure(c->scratch, sizeof(Scratch)) != AMR_OK) {
+    cudaGetLastError();
+    amr_destroy(c);
+    return AMR_ERR_OOM;
+  }
+  c->mc = make_mc_const();
+  *out = c;
+  return AMR_OK;
+}
+
+void amr_destroy(amr_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
+                    &c->cell_id, &c->scal, &c->view, &c->duals, &c->scratch, &c->stage_buf,
+                    &c->iso_buf, &c->seg_buf};
+  for (DevBuf* b : bufs) release(*b);
+  if (c->host_sc) cudaFreeHost(c->host_sc);
+  for (auto& v : c->pending)
+    for (auto& p : v) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int amr_set_stream(amr_ctx* c, void* cuda_stream) {
+  if (!c) return AMR_ERR_INVALID_ARG;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return AMR_OK;
+}
+
+int amr_sync(amr_ctx* c) {
+  if (!c) return AMR_ERR_INVALID_ARG;
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return AMR_OK;
+}
+
+int amr_upload(amr_ctx* c, const int32_t* xyz, const uint8_t* level, const float* scalar, int64_t n,
+               int flags) {
+  if (!c || n < 0 || (n > 0 && (!xyz || !level || !scalar))) return AMR_ERR_INVALID_ARG;
+  if (n > INT_MAX) return AMR_ERR_RANGE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  c->stage = 0;
+  c->n_dual = -1;
+  c->n = n;
+  if (flags & (AMR_HOST_PTRS | AMR_COPY)) {
+    AMR_TRY(ensure(c->own_xyz, (size_t)n * 12));
+    AMR_TRY(ensure(c->own_lvl, (size_t)n));
+    AMR_TRY(ensure(c->own_s, (size_t)n * 4));
+    const cudaMemcpyKind kind = (flags & AMR_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (n) {
+      AMR_CUDA(cudaMemcpyAsync(c->own_xyz.p, xyz, (size_t)n * 12, kind, c->stream));
+      AMR_CUDA(cudaMemcpyAsync(c->own_lvl.p, level, (size_t)n, kind, c->stream));
+      AMR_CUDA(cudaMemcpyAsync(c->own_s.p, scalar, (size_t)n * 4, kind, c->stream));
+    }
+    c->xyz = static_cast<const int*>(c->own_xyz.p);
+    c->lvl = static_cast<const unsigned char*>(c->own_lvl.p);
+    c->s = static_cast<const float*>(c->own_s.p);
+  } else {
+    c->xyz = xyz;
+    c->lvl = level;
+    c->s = scalar;
+  }
+  c->stage = 1;
+  return AMR_OK;
+}
+
+int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
+  if (!c) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 1) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  int logb = 3, block = 256, overlap = 0;
+  float alpha = 0.5f;
+  if (opts) {
+    if (opts->log2_brick) logb = opts->log2_brick;
+    if (opts->load_factor > 0.f) alpha = opts->load_factor;
+    if (opts->block_size) block = opts->block_size;
+    overlap = opts->check_overlap;
+  }
+  if ((logb != 2 && logb != 3) || alpha < 0.05f || alpha > 0.9f || block < 32 || block > 1024 ||
+      (block & 31))
+    return AMR_ERR_INVALID_ARG;
+  c->logb = logb;
+  c->alpha = alpha;
+  c->block = block;
+  c->check_overlap = overlap;
+  c->stage = 1;
+  c->n_dual = -1;
+  const long long n = c->n;
+  const int B3 = 1 << (3 * logb);
+  // Expected bricks: every brick at least 1/8 full; retry with a bigger
+  // table when the real count says otherwise.
+  unsigned long long want = (unsigned long long)((double)(n * 8 / B3 + 64) / alpha);
+  for (int attempt = 0;; ++attempt) {
+    c->hcap = pow2_at_least(want);
+    AMR_TRY(ensure(c->hkeys, c->hcap * 8));
+    AMR_TRY(ensure(c->hvals, c->hcap * 4));
+    AMR_TRY(ensure(c->bricks, c->hcap * 16));
+    AMR_CUDA(cudaMemsetAsync(c->hkeys.p, 0xFF, c->hcap * 8, c->stream));
+    AMR_TRY(reset_scratch(c));
+    if (n > 0) {
+      KernelTimer kt(c, KT_INSERT);
+      AMR_CUDA(launch_insert_bricks(logb, c->xyz, c->lvl, c->s, n,
+                                    static_cast<unsigned long long*>(c->hkeys.p),
+                                    static_cast<int*>(c->hvals.p), c->hcap - 1,
+                                    static_cast<int4*>(c->bricks.p), dev_sc(c),
+                                    grid_for(c, n, block, 2048 / block), block, c->stream));
+    }
+    AMR_TRY(read_scratch(c));
+    const Scratch& h = *c->host_sc;
+    const unsigned full = h.err & ERR_HASH_FULL;
+    const int rc = err_code(h.err & ~ERR_HASH_FULL);
+    if (rc != AMR_OK) return rc;
+    if (full || (double)h.n_bricks > (double)c->hcap * std::min(0.85, 2.0 * alpha)) {
+      if (attempt >= 4) return AMR_ERR_RANGE;
+      want = (unsigned long long)(std::max<double>((double)h.n_bricks, (double)want) * 4.0 / alpha);
+      continue;
+    }
+    c->n_bricks = (long long)h.n_bricks;
+    c->levels = n > 0 ? h.max_level + 1 : 0;
+    for (int a = 0; a < 3 && n > 0; ++a)
+      if ((long long)h.hi[a] - (long long)h.lo[a] >= (1ll << 21) || h.lo[a] < -(1 << 30) ||
+          h.hi[a] > (1 << 30))
+        return AMR_ERR_RANGE;
+    break;
+  }
+  c->n_slots = c->n_bricks * B3;
+  if (c->n_slots >= (long long)INT_MAX) return AMR_ERR_RANGE;
+  AMR_TRY(ensure(c->cell_id, (size_t)c->n_slots * 4));
+  AMR_TRY(ensure(c->scal, (size_t)c->n_slots * 4));
+  AMR_TRY(ensure(c->view, (size_t)c->n_slots * 4));
+  if (c->n_slots) {
+    AMR_CUDA(cudaMemsetAsync(c->cell_id.p, 0xFF, (size_t)c->n_slots * 4, c->stream));
+    const Locator L = make_locator(c);
+    {
+      KernelTimer kt(c, KT_SCATTER);
+      AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, L, static_cast<int*>(c->cell_id.p),
+                                    static_cast<float*>(c->scal.p), dev_sc(c),
+                                    grid_for(c, n, block, 2048 / block), block, c->stream));
+    }
+    {
+      KernelTimer kt(c, KT_RESOLVE);
+      AMR_CUDA(launch_resolve_views(logb, L, static_cast<unsigned*>(c->view.p), c->n_slots, overlap,
+                                    dev_sc(c), grid_for(c, c->n_slots, block, 2048 / block), block,
+                                    c->stream));
+    }
+    AMR_TRY(read_scratch(c));
+    const int rc = err_code(c->host_sc->err);
+    if (rc != AMR_OK) return rc;
+  }
+  c->stage = 2;
+  return AMR_OK;
+}
+
+int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
+  if (!c || !n_dual) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 2) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  long long cap = std::max(c->dual_cap, c->n + c->n / 4 + 1024);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    AMR_TRY(ensure(c->duals, (size_t)cap * 32));
+    c->dual_cap = (long long)(c->duals.bytes / 32);
+    AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->n_dual, 0, sizeof(unsigned long long), c->stream));
+    {
+      KernelTimer kt(c, KT_DUAL);
+      AMR_CUDA(launch_dual_cells(c->logb, make_locator(c), c->n_bricks, static_cast<uint4*>(c->duals.p),
+                                 c->dual_cap, dev_sc(c), c->stream));
+    }
+    AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_dual, &dev_sc(c)->n_dual, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+    AMR_CUDA(cudaStreamSynchronize(c->stream));
+    const long long nd = (long long)c->host_sc->n_dual;
+    if (nd <= c->dual_cap) {
+      c->n_dual = nd;
+      c->stage = 3;
+      *n_dual = nd;
+      return AMR_OK;
+    }
+    cap = nd;  // exact count known: grow and run again
+  }
+  return AMR_ERR_CUDA;
+}
+
+int amr_get_duals(amr_ctx* c, int32_t* out, int64_t cap, int flags) {
+  if (!c || (!out && cap > 0) || cap < 0) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  if (cap < c->n_dual) return AMR_ERR_CAPACITY;
+  AMR_CUDA(cudaSetDevice(c->device));
+  if (c->n_dual == 0) return AMR_OK;
+  const size_t bytes = (size_t)c->n_dual * 32;
+  int* dst = reinterpret_cast<int*>(out);
+  if (flags & AMR_HOST_PTRS) {
+    AMR_TRY(ensure(c->stage_buf, bytes));
+    dst = static_cast<int*>(c->stage_buf.p);
+  }
+  {
+    KernelTimer kt(c, KT_GET_DUALS);
+    AMR_CUDA(launch_get_duals(static_cast<const uint4*>(c->duals.p), c->n_dual,
+                              static_cast<const int*>(c->cell_id.p), dst, grid_for(c, 2 * c->n_dual, 256, 8),
+                              c->stream));
+  }
+  AMR_TRY(deliver(c, out, dst, bytes, flags));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return AMR_OK;
+}
+
+int amr_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t* n_tris, int flags) {
+  if (!c || !n_tris || cap < 0 || (cap > 0 && !tris)) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  float* dst = tris;
+  if ((flags & AMR_HOST_PTRS) && cap > 0) {
+    AMR_TRY(ensure(c->stage_buf, (size_t)cap * 36));
+    dst = static_cast<float*>(c->stage_buf.p);
+  }
+  unsigned long long* counter = &dev_sc(c)->n_tri[0];
+  AMR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), c->stream));
+  {
+    KernelTimer kt(c, KT_MC);
+    AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), c->n_dual, iso, dst,
+                       cap, counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream));
+  }
+  AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], counter, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  const long long nt = (long long)c->host_sc->n_tri[0];
+  *n_tris = nt;
+  if (flags & AMR_HOST_PTRS) {
+    AMR_TRY(deliver(c, tris, dst, (size_t)std::min<long long>(nt, cap) * 36, flags));
+    AMR_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return nt > cap ? AMR_ERR_CAPACITY : AMR_OK;
+}
+
+int amr_iso_cases(amr_ctx* c, float iso, uint8_t* cases, uint8_t* ntri, int flags) {
+  if (!c || (!cases && !ntri)) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  const long long nd = c->n_dual;
+  unsigned char* dc = cases;
+  unsigned char* dn = ntri;
+  if (flags & AMR_HOST_PTRS) {
+    AMR_TRY(ensure(c->stage_buf, (size_t)nd * 2 + 256));
+    dc = cases ? static_cast<unsigned char*>(c->stage_buf.p) : nullptr;
+    dn = ntri ? static_cast<unsigned char*>(c->stage_buf.p) + nd : nullptr;
+  }
+  {
+    KernelTimer kt(c, KT_MC_CASES);
+    AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), nd, iso, nullptr, 0,
+                       nullptr, dc, dn, c->mc, grid_for(c, nd, 256, 8), c->stream));
+  }
+  if (cases) AMR_TRY(deliver(c, cases, dc, (size_t)nd, flags));
+  if (ntri) AMR_TRY(deliver(c, ntri, dn, (size_t)nd, flags));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return AMR_OK;
+}
+
+int amr_iso_batch(amr_ctx* c, const float* isos, int n_iso, float* tris, int64_t cap, int64_t* offsets,
+                  int flags) {
+  if (!c || !isos || !offsets || n_iso < 1 || n_iso > kMaxIso || cap < 0 || (cap > 0 && !tris))
+    return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  const long long nd = c->n_dual;
+  AMR_TRY(ensure(c->iso_buf, sizeof(float) * kMaxIso));
+  AMR_TRY(ensure(c->seg_buf, sizeof(long long) * (kMaxIso + 1)));
+  float* d_iso = static_cast<float*>(c->iso_buf.p);
+  AMR_CUDA(cudaMemcpyAsync(d_iso, isos, sizeof(float) * n_iso, cudaMemcpyHostToDevice, c->stream));
+  AMR_CUDA(cudaMemsetAsync(dev_sc(c)->n_tri, 0, sizeof(unsigned long long) * kMaxIso, c->stream));
+  const Locator L = make_locator(c);
+  const uint4* du = static_cast<const uint4*>(c->duals.p);
+  const int grid = c->sm_count * 8;
+  {
+    KernelTimer kt(c, KT_BATCH_COUNT);
+    AMR_CUDA(launch_mc_batch_count(c->logb, L, du, nd, d_iso, n_iso, dev_sc(c), c->mc,
+                                   grid_for(c, nd, 256, 8), c->stream));
+  }
+  AMR_CUDA(cudaMemcpyAsync(c->host_sc->n_tri, dev_sc(c)->n_tri, sizeof(unsigned long long) * n_iso,
+                           cudaMemcpyDeviceToHost, c->stream));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  long long run = 0;
+  for (int k = 0; k < n_iso; ++k) {
+    offsets[k] = run;
+    run += (long long)c->host_sc->n_tri[k];
+  }
+  offsets[n_iso] = run;
+  if (run > cap) return AMR_ERR_CAPACITY;
+  float* dst = tris;
+  if (flags & AMR_HOST_PTRS) {
+    AMR_TRY(ensure(c->stage_buf, (size_t)std::max<long long>(run, 1) * 36));
+    dst = static_cast<float*>(c->stage_buf.p);
+  }
+  long long* d_off = static_cast<long long*>(c->seg_buf.p);
+  AMR_CUDA(cudaMemcpyAsync(d_off, offsets, sizeof(long long) * (n_iso + 1), cudaMemcpyHostToDevice,
+                           c->stream));
+  AMR_CUDA(cudaMemsetAsync(dev_sc(c)->n_tri, 0, sizeof(unsigned long long) * kMaxIso, c->stream));
+  AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->tile, 0, sizeof(unsigned long long), c->stream));
+  {
+    KernelTimer kt(c, KT_BATCH_EMIT);
+    AMR_CUDA(launch_mc_batch_emit(c->logb, L, du, nd, d_iso, n_iso, dst, d_off, dev_sc(c), c->mc,
+                                  grid, 4096, c->stream));
+  }
+  if (flags & AMR_HOST_PTRS) AMR_TRY(deliver(c, tris, dst, (size_t)run * 36, flags));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return AMR_OK;
+}
+
+int amr_get_info(amr_ctx* c, amr_info* info) {
+  if (!c || !info) return AMR_ERR_INVALID_ARG;
+  info->n_cells = c->n;
+  info->n_bricks = c->stage >= 2 ? c->n_bricks : 0;
+  info->n_slots = c->stage >= 2 ? c->n_slots : 0;
+  info->n_dual = c->stage >= 3 ? c->n_dual : -1;
+  info->n_levels = c->stage >= 2 ? c->levels : 0;
+  info->log2_brick = c->logb;
+  const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
+                          &c->cell_id, &c->scal, &c->view, &c->duals, &c->scratch, &c->stage_buf,
+                          &c->iso_buf, &c->seg_buf};
+  long long total = 0;
+  for (const DevBuf* b : bufs) total += (long long)held(*b);
+  info->device_bytes = total;
+  return AMR_OK;
+}
+
+int amr_enable_timing(amr_ctx* c, int on) {
+  if (!c) return AMR_ERR_INVALID_ARG;
+  c->timing = on != 0;
+  return AMR_OK;
+}
+
+int amr_kernel_times(amr_ctx* c, double* ms, int64_t* launches, int n) {
+  if (!c) return AMR_ERR_INVALID_ARG;
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < KT_COUNT; ++k) {
+    for (auto& p : c->pending[k]) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, p.first, p.second);
+      c->ms_acc[k] += t;
+      c->ev_pool.push_back(p.first);
+      c->ev_pool.push_back(p.second);
+    }
+    c->pending[k].clear();
+    if (k < n) {
+      if (ms) ms[k] = c->ms_acc[k];
+      if (launches) launches[k] = c->launches[k];
+    }
+    c->ms_acc[k] = 0;
+    c->launches[k] = 0;
+  }
+  return KT_COUNT;
+}
+
+const char* amr_kernel_name(int k) { return (k >= 0 && k < KT_COUNT) ? kKernelNames[k] : nullptr; }
+
+}  // extern "C"

@@ -1,0 +1,802 @@
+// CUDA kernels (sm_103a) for AMR dual cells and iso-surfaces (Wald, Sec. 3-5).
+//
+// Data layout in HBM (one data set):
+//   input        xyz[n][3] int32, level[n] u8, scalar[n] f32 (caller order)
+//   brick hash   hkeys[hcap] u64 key = (level, brick coords) -> hvals[hcap] brick index
+//   bricks       bricks[n_bricks] int4 = lower corner of the brick (finest
+//                units) and its level; a level-l brick covers B^3 logical
+//                level-l cells, B = 2^LOGB
+//   slots        one per logical cell of every brick, Morton order inside a
+//                brick: cell_id[] (input index or -1), scal[] (its scalar),
+//                view[] (the slot of the actual cell containing the logical
+//                cell: itself, a coarser cell, or kReject)
+//   dual cells   duals[D] = 2 x uint4: the 8 vertex slots, order ex+2ey+4ez
+//   triangles    tris[T][3][3] f32
+//
+// snap() of Sec. 3.2 becomes: find the brick of the query at the query's
+// level (one hash probe), read the slot's view. A missing brick at level l
+// means no level-l cell near the query; the first existing brick at a
+// coarser level then holds the answer, because an aligned level-l brick lies
+// inside one aligned brick of every coarser level.
+
+#include <climits>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace amriso {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// SplitMix64 output finaliser (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014), used as the bucket hash.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Key of the level-l brick containing finest-level point (x,y,z). Brick
+// coordinates are kept modulo 2^20, which is exact because extents are
+// below 2^21 finest units.
+template <int LOGB>
+__device__ __forceinline__ unsigned long long brick_key(int x, int y, int z, int l) {
+  const int sh = l + LOGB;
+  const unsigned long long bx = (unsigned)(x >> sh) & 0xFFFFFu;
+  const unsigned long long by = (unsigned)(y >> sh) & 0xFFFFFu;
+  const unsigned long long bz = (unsigned)(z >> sh) & 0xFFFFFu;
+  return ((unsigned long long)l << 60) | (bz << 40) | (by << 20) | bx;
+}
+
+template <int LOGB>
+__device__ __forceinline__ unsigned spread(unsigned v) {
+  unsigned r = 0;
+#pragma unroll
+  for (int b = 0; b < LOGB; ++b) r |= ((v >> b) & 1u) << (3 * b);
+  return r;
+}
+
+template <int LOGB>
+__device__ __forceinline__ int compact(unsigned m) {
+  unsigned r = 0;
+#pragma unroll
+  for (int b = 0; b < LOGB; ++b) r |= ((m >> (3 * b)) & 1u) << b;
+  return (int)r;
+}
+
+// Morton index, inside its level-l brick, of the logical level-l cell
+// containing (x,y,z).
+template <int LOGB>
+__device__ __forceinline__ unsigned local_index(int x, int y, int z, int l) {
+  constexpr unsigned M = (1u << LOGB) - 1u;
+  return spread<LOGB>((unsigned)(x >> l) & M) | (spread<LOGB>((unsigned)(y >> l) & M) << 1) |
+         (spread<LOGB>((unsigned)(z >> l) & M) << 2);
+}
+
+__device__ __forceinline__ int find_brick(const Locator& L, unsigned long long key) {
+  unsigned long long h = mix64(key) & L.hmask;
+  for (unsigned long long p = 0; p <= L.hmask; ++p) {
+    const unsigned long long k = __ldg(L.hkeys + h);
+    if (k == key) return __ldg(L.hvals + h);
+    if (k == kEmptyKey) return -1;
+    h = (h + 1) & L.hmask;
+  }
+  return -1;
+}
+
+// Lower corner and level of the cell stored in `slot`.
+template <int LOGB>
+__device__ __forceinline__ int4 slot_cell(const int4* __restrict__ bricks, unsigned slot) {
+  const int4 b = __ldg(bricks + (slot >> (3 * LOGB)));
+  const unsigned loc = slot & ((1u << (3 * LOGB)) - 1u);
+  return make_int4(b.x + (compact<LOGB>(loc) << b.w), b.y + (compact<LOGB>(loc >> 1) << b.w),
+                   b.z + (compact<LOGB>(loc >> 2) << b.w), b.w);
+}
+
+__device__ __forceinline__ unsigned warp_or(unsigned v) { return __reduce_or_sync(kFull, v); }
+
+// ---------------------------------------------------------------------------
+// Locator build (Sec. 3.2)
+// ---------------------------------------------------------------------------
+
+// Pass 1 over the cells: validate, take the bounding box and the deepest
+// level, and insert every cell's brick key into the hash table. The CAS
+// winner of a key numbers the brick and records its corner and level.
+template <int LOGB>
+__global__ void __launch_bounds__(1024) k_insert_bricks(
+    const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
+    const float* __restrict__ s, long long n, unsigned long long* hkeys, int* hvals,
+    unsigned long long hmask, int4* bricks, Scratch* sc) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lo0 = INT_MAX, lo1 = INT_MAX, lo2 = INT_MAX;
+  int hi0 = INT_MIN, hi1 = INT_MIN, hi2 = INT_MIN;
+  int ml = 0;
+  unsigned err = 0;
+  for (long long base = wid * 32; base < n; base += nwarps * 32) {
+    const long long i = base + lane;
+    unsigned long long key = kEmptyKey;
+    int x = 0, y = 0, z = 0, l = 0;
+    if (i < n) {
+      x = xyz[3 * i];
+      y = xyz[3 * i + 1];
+      z = xyz[3 * i + 2];
+      l = lvl[i];
+      if (!isfinite(s[i])) err |= ERR_NONFINITE;
+      if (l > kMaxLevel) {
+        err |= ERR_RANGE;
+      } else if ((x | y | z) & ((1 << l) - 1)) {
+        err |= ERR_UNALIGNED;
+      } else {
+        const long long w = 1ll << l;
+        lo0 = min(lo0, x);
+        lo1 = min(lo1, y);
+        lo2 = min(lo2, z);
+        hi0 = max(hi0, (int)min((long long)x + w, (long long)INT_MAX));
+        hi1 = max(hi1, (int)min((long long)y + w, (long long)INT_MAX));
+        hi2 = max(hi2, (int)min((long long)z + w, (long long)INT_MAX));
+        ml = max(ml, l);
+        key = brick_key<LOGB>(x, y, z, l);
+      }
+    }
+    const unsigned peers = __match_any_sync(kFull, key);
+    if (key != kEmptyKey && lane == __ffs(peers) - 1) {
+      unsigned long long h = mix64(key) & hmask;
+      bool done = false;
+      // a table this crowded is rebuilt larger by the host: fail fast
+      const unsigned long long limit = hmask < 4095ull ? hmask + 1 : 4096ull;
+      for (unsigned long long p = 0; p < limit; ++p) {
+        const unsigned long long cur = __ldcg(hkeys + h);
+        if (cur == key) { done = true; break; }
+        if (cur == kEmptyKey) {
+          const unsigned long long prev = atomicCAS(hkeys + h, kEmptyKey, key);
+          if (prev == kEmptyKey) {
+            const unsigned long long bi = atomicAdd(&sc->n_bricks, 1ull);
+            hvals[h] = (int)bi;
+            const int m = ~((1 << (l + LOGB)) - 1);
+            bricks[bi] = make_int4(x & m, y & m, z & m, l);
+            done = true;
+            break;
+          }
+          if (prev == key) { done = true; break; }
+        }
+        h = (h + 1) & hmask;
+      }
+      if (!done) err |= ERR_HASH_FULL;
+    }
+  }
+  // block reduction, then one set of atomics per block
+  __shared__ int red[8][32];
+  const int w = threadIdx.x >> 5;
+  lo0 = __reduce_min_sync(kFull, lo0);
+  lo1 = __reduce_min_sync(kFull, lo1);
+  lo2 = __reduce_min_sync(kFull, lo2);
+  hi0 = __reduce_max_sync(kFull, hi0);
+  hi1 = __reduce_max_sync(kFull, hi1);
+  hi2 = __reduce_max_sync(kFull, hi2);
+  ml = __reduce_max_sync(kFull, ml);
+  err = warp_or(err);
+  if (lane == 0) {
+    red[0][w] = lo0; red[1][w] = lo1; red[2][w] = lo2;
+    red[3][w] = hi0; red[4][w] = hi1; red[5][w] = hi2;
+    red[6][w] = ml;  red[7][w] = (int)err;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    const bool ok = lane < nw;
+    int a0 = ok ? red[0][lane] : INT_MAX, a1 = ok ? red[1][lane] : INT_MAX,
+        a2 = ok ? red[2][lane] : INT_MAX;
+    int b0 = ok ? red[3][lane] : INT_MIN, b1 = ok ? red[4][lane] : INT_MIN,
+        b2 = ok ? red[5][lane] : INT_MIN;
+    int m = ok ? red[6][lane] : 0;
+    unsigned e = ok ? (unsigned)red[7][lane] : 0u;
+    a0 = __reduce_min_sync(kFull, a0);
+    a1 = __reduce_min_sync(kFull, a1);
+    a2 = __reduce_min_sync(kFull, a2);
+    b0 = __reduce_max_sync(kFull, b0);
+    b1 = __reduce_max_sync(kFull, b1);
+    b2 = __reduce_max_sync(kFull, b2);
+    m = __reduce_max_sync(kFull, m);
+    e = warp_or(e);
+    if (lane == 0) {
+      if (a0 != INT_MAX) {
+        atomicMin(&sc->lo[0], a0); atomicMin(&sc->lo[1], a1); atomicMin(&sc->lo[2], a2);
+        atomicMax(&sc->hi[0], b0); atomicMax(&sc->hi[1], b1); atomicMax(&sc->hi[2], b2);
+        atomicMax(&sc->max_level, m);
+      }
+      if (e) atomicOr(&sc->err, e);
+    }
+  }
+}
+
+// Pass 2 over the cells: put every cell into its brick slot. Two cells in one
+// slot are a duplicate label (i,j,k;l).
+template <int LOGB>
+__global__ void __launch_bounds__(1024) k_scatter_cells(
+    const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
+    const float* __restrict__ s, long long n, Locator L, int* cell_id, float* scal, Scratch* sc) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  unsigned err = 0;
+  for (long long base = wid * 32; base < n; base += nwarps * 32) {
+    const long long i = base + lane;
+    unsigned long long key = kEmptyKey;
+    int x = 0, y = 0, z = 0, l = 0;
+    float v = 0.f;
+    if (i < n) {
+      x = xyz[3 * i];
+      y = xyz[3 * i + 1];
+      z = xyz[3 * i + 2];
+      l = lvl[i];
+      v = s[i];
+      if (l <= kMaxLevel) key = brick_key<LOGB>(x, y, z, l);
+    }
+    const unsigned peers = __match_any_sync(kFull, key);
+    const int leader = __ffs(peers) - 1;
+    int bi = -1;
+    if (key != kEmptyKey && lane == leader) bi = find_brick(L, key);
+    bi = __shfl_sync(kFull, bi, leader);
+    if (key != kEmptyKey) {
+      if (bi < 0) {
+        err |= ERR_HASH_FULL;
+      } else {
+        const long long slot = ((long long)bi << (3 * LOGB)) | local_index<LOGB>(x, y, z, l);
+        if (atomicCAS(cell_id + slot, -1, (int)i) != -1) err |= ERR_DUPLICATE;
+        scal[slot] = v;
+      }
+    }
+  }
+  err = warp_or(err);
+  if (lane == 0 && err) atomicOr(&sc->err, err);
+}
+
+// Pass over the slots: resolve every logical cell of every brick to the
+// actual cell containing it - its own occupant, else the first occupied slot
+// at a coarser level, else kReject (finer cells or a hole). With
+// check_overlap, an occupied slot that is also covered by a coarser cell
+// flags ERR_OVERLAP.
+template <int LOGB>
+__global__ void __launch_bounds__(1024) k_resolve_views(Locator L, unsigned* view, long long n_slots,
+                                                       int check_overlap, Scratch* sc) {
+  unsigned err = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x; slot < n_slots;
+       slot += stride) {
+    const int4 c = slot_cell<LOGB>(L.bricks, (unsigned)slot);
+    const int id = L.cell_id[slot];
+    unsigned v = id >= 0 ? (unsigned)slot : kReject;
+    if (id < 0 || check_overlap) {
+      for (int lv = c.w + 1; lv < L.levels; ++lv) {
+        const int bj = find_brick(L, brick_key<LOGB>(c.x, c.y, c.z, lv));
+        if (bj < 0) continue;
+        const unsigned s2 = ((unsigned)bj << (3 * LOGB)) | local_index<LOGB>(c.x, c.y, c.z, lv);
+        if (__ldg(L.cell_id + s2) >= 0) {
+          if (id >= 0) err |= ERR_OVERLAP;
+          else v = s2;
+          break;
+        }
+      }
+    }
+    view[slot] = v;
+  }
+  if (err) atomicOr(&sc->err, err);
+}
+
+// ---------------------------------------------------------------------------
+// Dual cells (Sec. 4.2 - 4.4)
+// ---------------------------------------------------------------------------
+
+// 27-bit masks over the 3x3x3 neighbourhood (offset o = ox + 3 oy + 9 oz,
+// o in {0,1,2}^3 relative to the cell minus one) of the 8 vertices of dual
+// delta (vertices at offsets delta + e) and of the vertices with e below the
+// cell's own position e_S = 1 - delta.
+struct DualMasks {
+  unsigned all[8];
+  unsigned lower[8];
+};
+
+__host__ __device__ constexpr DualMasks make_dual_masks() {
+  DualMasks m{};
+  for (int d = 0; d < 8; ++d) {
+    const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+    const int es = 7 - d;
+    unsigned all = 0, lower = 0;
+    for (int e = 0; e < 8; ++e) {
+      const int o = (dx + (e & 1)) + 3 * (dy + ((e >> 1) & 1)) + 9 * (dz + (e >> 2));
+      all |= 1u << o;
+      if (e < es) lower |= 1u << o;
+    }
+    m.all[d] = all;
+    m.lower[d] = lower;
+  }
+  return m;
+}
+
+__constant__ DualMasks c_masks = make_dual_masks();
+
+// One CTA per brick, one thread per brick slot. The CTA loads the brick's
+// resolved views plus a one-cell halo ((B+2)^3 entries, from the 26
+// neighbouring bricks of the same level or the first coarser brick that
+// covers them) into shared memory; each thread then decides the 8 duals of
+// its cell: a dual is emitted iff every vertex exists (rule 1), none is finer
+// (rule 2, finer regions resolve to kReject) and every same-level vertex
+// comes after the cell in (z,y,x) order (rule 3). Survivors are compacted
+// with one atomic per CTA.
+template <int LOGB>
+__global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
+    Locator L, long long n_bricks, uint4* __restrict__ duals, long long cap, Scratch* sc) {
+  constexpr int B = 1 << LOGB;
+  constexpr int R = B + 2;
+  constexpr int NT = B * B * B;
+  constexpr int NR = R * R * R;
+  constexpr int NW = (NT + 31) / 32;
+  __shared__ unsigned rv[NR];
+  __shared__ unsigned char rs[NR];
+  __shared__ int nb_bi[27];
+  __shared__ int nb_lv[27];
+  __shared__ unsigned wsum[NW];
+  __shared__ unsigned long long cta_base;
+  const int t = threadIdx.x;
+  const int lane = t & 31, wp = t >> 5;
+  const int px = compact<LOGB>(t), py = compact<LOGB>(t >> 1), pz = compact<LOGB>(t >> 2);
+  const int c0 = px + R * (py + R * pz);   // neighbourhood origin (cell - 1) in the region
+  for (long long bi = blockIdx.x; bi < n_bricks; bi += gridDim.x) {
+    const int4 b = __ldg(L.bricks + bi);
+    const int l = b.w;
+    if (t < 27) {
+      int fb = -1, fl = l;
+      if (t == 13) {
+        fb = (int)bi;
+      } else {
+        const int ext = B << l;
+        const int qx = b.x + (t % 3 - 1) * ext, qy = b.y + ((t / 3) % 3 - 1) * ext,
+                  qz = b.z + (t / 9 - 1) * ext;
+        for (int lv = l; lv < L.levels; ++lv) {
+          const int bj = find_brick(L, brick_key<LOGB>(qx, qy, qz, lv));
+          if (bj >= 0) { fb = bj; fl = lv; break; }
+        }
+      }
+      nb_bi[t] = fb;
+      nb_lv[t] = fl;
+    }
+    __syncthreads();
+    for (int r = t; r < NR; r += NT) {
+      const int rx = r % R, ry = (r / R) % R, rz = r / (R * R);
+      const int nbi = (rx == 0 ? 0 : (rx == R - 1 ? 2 : 1)) + 3 * (ry == 0 ? 0 : (ry == R - 1 ? 2 : 1)) +
+                      9 * (rz == 0 ? 0 : (rz == R - 1 ? 2 : 1));
+      const int fb = nb_bi[nbi];
+      unsigned v = kReject;
+      unsigned char same = 0;
+      if (fb >= 0) {
+        const int lv = nb_lv[nbi];
+        const int x = b.x + ((rx - 1) << l), y = b.y + ((ry - 1) << l), z = b.z + ((rz - 1) << l);
+        const unsigned s2 = ((unsigned)fb << (3 * LOGB)) | local_index<LOGB>(x, y, z, lv);
+        v = __ldg(L.view + s2);
+        same = (lv == l) && (v == s2);
+      }
+      rv[r] = v;
+      rs[r] = same;
+    }
+    __syncthreads();
+    unsigned emit = 0;
+    if (rs[c0 + 1 + R + R * R]) {   // this slot holds an actual level-l cell
+      unsigned exist = 0, samem = 0;
+#pragma unroll
+      for (int o = 0; o < 27; ++o) {
+        const int r = c0 + (o % 3) + R * ((o / 3) % 3) + R * R * (o / 9);
+        exist |= (rv[r] != kReject ? 1u : 0u) << o;
+        samem |= (unsigned)rs[r] << o;
+      }
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const bool ok = ((exist & c_masks.all[d]) == c_masks.all[d]) && !(samem & c_masks.lower[d]);
+        emit |= (ok ? 1u : 0u) << d;
+      }
+    }
+    // CTA-wide exclusive scan of the per-thread dual counts
+    const unsigned cnt = __popc(emit);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wp] = incl;
+    __syncthreads();
+    if (t == 0) {
+      unsigned run = 0;
+      for (int w = 0; w < NW; ++w) {
+        const unsigned x = wsum[w];
+        wsum[w] = run;
+        run += x;
+      }
+      cta_base = run ? atomicAdd(&sc->n_dual, (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    long long idx = (long long)cta_base + wsum[wp] + incl - cnt;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      if (!((emit >> d) & 1u)) continue;
+      const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+      unsigned v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        v[e] = rv[c0 + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2))];
+      if (idx < cap) {
+        duals[2 * idx] = make_uint4(v[0], v[1], v[2], v[3]);
+        duals[2 * idx + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+      }
+      ++idx;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Marching Cubes on dual cells (Sec. 5, 5.1, 5.2)
+// ---------------------------------------------------------------------------
+
+struct McShared {
+  unsigned long long packed[256];
+  unsigned char count[256];
+};
+
+__device__ __forceinline__ void load_mc(McShared& sh, const McConst& mc) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    sh.packed[i] = mc.packed[i];
+    sh.count[i] = mc.count[i];
+  }
+}
+
+__device__ __forceinline__ void load_dual(const uint4* __restrict__ duals, long long d, unsigned v[8]) {
+  const uint4 a = __ldg(duals + 2 * d);
+  const uint4 c = __ldg(duals + 2 * d + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
+}
+
+// Edge key (unordered pair of cells) of hexahedron edge k.
+__device__ __forceinline__ unsigned long long edge_key(const unsigned v[8], int k,
+                                                       unsigned long long ea, unsigned long long eb) {
+  const unsigned a = v[(ea >> (4 * k)) & 15], b = v[(eb >> (4 * k)) & 15];
+  return a < b ? ((unsigned long long)a << 32) | b : ((unsigned long long)b << 32) | a;
+}
+
+// Bit t set when triangle t of the case has three different edge keys.
+__device__ __forceinline__ unsigned kept_triangles(unsigned long long packed, int cnt, const unsigned v[8],
+                                                   unsigned long long ea, unsigned long long eb) {
+  unsigned keep = 0;
+  for (int t = 0; t < cnt; ++t) {
+    const unsigned long long k0 = edge_key(v, (int)((packed >> (12 * t)) & 15), ea, eb);
+    const unsigned long long k1 = edge_key(v, (int)((packed >> (12 * t + 4)) & 15), ea, eb);
+    const unsigned long long k2 = edge_key(v, (int)((packed >> (12 * t + 8)) & 15), ea, eb);
+    if (k0 != k1 && k1 != k2 && k0 != k2) keep |= 1u << t;
+  }
+  return keep;
+}
+
+// Interpolated vertex on the edge between cells a and b: from the cell with
+// the lower (z,y,x) corner, t = (iso - sa) / (sb - sa), P = ca + t (cb - ca),
+// every operation rounded on its own (no contraction).
+__device__ __forceinline__ float3 edge_vertex(int4 pa, float sa, int4 pb, float sb, float iso) {
+  const bool swap = (pb.z < pa.z) || (pb.z == pa.z && (pb.y < pa.y || (pb.y == pa.y && pb.x < pa.x)));
+  if (swap) {
+    const int4 tp = pa; pa = pb; pb = tp;
+    const float ts = sa; sa = sb; sb = ts;
+  }
+  const float ha = __fmul_rn(__int2float_rn(1 << pa.w), 0.5f);
+  const float hb = __fmul_rn(__int2float_rn(1 << pb.w), 0.5f);
+  const float d = __fsub_rn(sb, sa);
+  const float t = __fdiv_rn(__fsub_rn(iso, sa), d);
+  float3 p;
+  {
+    const float ca = __fadd_rn(__int2float_rn(pa.x), ha), cb = __fadd_rn(__int2float_rn(pb.x), hb);
+    p.x = __fadd_rn(ca, __fmul_rn(t, __fsub_rn(cb, ca)));
+  }
+  {
+    const float ca = __fadd_rn(__int2float_rn(pa.y), ha), cb = __fadd_rn(__int2float_rn(pb.y), hb);
+    p.y = __fadd_rn(ca, __fmul_rn(t, __fsub_rn(cb, ca)));
+  }
+  {
+    const float ca = __fadd_rn(__int2float_rn(pa.z), ha), cb = __fadd_rn(__int2float_rn(pb.z), hb);
+    p.z = __fadd_rn(ca, __fmul_rn(t, __fsub_rn(cb, ca)));
+  }
+  return p;
+}
+
+// Warp-level append: exclusive prefix of k over the warp plus one atomic per
+// warp; returns this lane's first output index.
+__device__ __forceinline__ long long warp_append(unsigned k, unsigned long long* counter) {
+  const int lane = threadIdx.x & 31;
+  unsigned incl = k;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned total = __shfl_sync(kFull, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, (unsigned long long)total);
+  base = __shfl_sync(kFull, base, 31);
+  return (long long)base + incl - k;
+}
+
+template <int LOGB>
+__device__ __forceinline__ void write_triangles(const Locator& L, const unsigned v[8], const float sv[8],
+                                                float iso, unsigned long long packed, unsigned keep,
+                                                long long idx, long long cap, float* __restrict__ tris,
+                                                unsigned long long ea, unsigned long long eb) {
+  int4 p[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) p[e] = slot_cell<LOGB>(L.bricks, v[e]);
+  for (int t = 0; t < 5; ++t) {
+    if (!((keep >> t) & 1u)) continue;
+    if (idx < cap) {
+      float* out = tris + 9 * idx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int k = (int)((packed >> (12 * t + 4 * c)) & 15);
+        const int a = (int)((ea >> (4 * k)) & 15), b = (int)((eb >> (4 * k)) & 15);
+        const float3 q = edge_vertex(p[a], sv[a], p[b], sv[b], iso);
+        out[3 * c + 0] = q.x;
+        out[3 * c + 1] = q.y;
+        out[3 * c + 2] = q.z;
+      }
+    }
+    ++idx;
+  }
+}
+
+// One thread per dual cell: gather the 8 vertex scalars, build the case
+// index (bit e set iff s_e > iso), keep the case's triangles that have three
+// different edge keys, append them with one atomic per warp and write their
+// interpolated vertices. Optionally writes per-dual case and triangle count.
+template <int LOGB, bool EMIT, bool CASES>
+__global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
+                                            float iso, float* __restrict__ tris, long long cap,
+                                            unsigned long long* counter, unsigned char* cases,
+                                            unsigned char* ntri, const __grid_constant__ McConst mc) {
+  __shared__ McShared sh;
+  load_mc(sh, mc);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (long long base = wid * 32; base < nd; base += nwarps * 32) {
+    const long long d = base + lane;
+    unsigned v[8];
+    float sv[8];
+    int cas = 0;
+    unsigned keep = 0;
+    if (d < nd) {
+      load_dual(duals, d, v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        sv[e] = __ldg(L.scal + v[e]);
+        cas |= (sv[e] > iso ? 1 : 0) << e;
+      }
+      const int cnt = sh.count[cas];
+      if (cnt) keep = kept_triangles(sh.packed[cas], cnt, v, mc.edge_a, mc.edge_b);
+      if (CASES) {
+        if (cases) cases[d] = (unsigned char)cas;
+        if (ntri) ntri[d] = (unsigned char)__popc(keep);
+      }
+    }
+    if (EMIT) {
+      if (__ballot_sync(kFull, keep != 0) == 0) continue;
+      const long long idx = warp_append(__popc(keep), counter);
+      if (keep)
+        write_triangles<LOGB>(L, v, sv, iso, sh.packed[cas], keep, idx, cap, tris, mc.edge_a, mc.edge_b);
+    }
+  }
+}
+
+// Batched iso-values, count pass: per-iso kept-triangle totals, accumulated
+// in shared memory and added to the global counters once per CTA.
+template <int LOGB>
+__global__ void __launch_bounds__(256) k_mc_batch_count(Locator L, const uint4* __restrict__ duals,
+                                                        long long nd, const float* __restrict__ isos,
+                                                        int n_iso, Scratch* sc,
+                                                        const __grid_constant__ McConst mc) {
+  __shared__ McShared sh;
+  __shared__ unsigned long long cnt_sh[kMaxIso];
+  __shared__ float iso_sh[kMaxIso];
+  load_mc(sh, mc);
+  for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
+    cnt_sh[k] = 0;
+    iso_sh[k] = isos[k];
+  }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < nd; d += stride) {
+    unsigned v[8];
+    float sv[8];
+    load_dual(duals, d, v);
+    float mn = 3.4e38f, mx = -3.4e38f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      sv[e] = __ldg(L.scal + v[e]);
+      mn = fminf(mn, sv[e]);
+      mx = fmaxf(mx, sv[e]);
+    }
+    for (int k = 0; k < n_iso; ++k) {
+      const float iso = iso_sh[k];
+      if (!(mx > iso) || mn > iso) continue;   // case 0 or 255
+      int cas = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) cas |= (sv[e] > iso ? 1 : 0) << e;
+      const unsigned keep = kept_triangles(sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
+      if (keep) atomicAdd(&cnt_sh[k], (unsigned long long)__popc(keep));
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n_iso; k += blockDim.x)
+    if (cnt_sh[k]) atomicAdd(&sc->n_tri[k], cnt_sh[k]);
+}
+
+// Batched iso-values, emit pass: a persistent grid pulls tiles of dual cells
+// from a device counter (no waiting on other CTAs); every dual's vertices and
+// scalars are read once and tested against all iso-values; iso k's triangles
+// go to its own segment tris[seg_off[k] ...] through counter n_tri[k].
+template <int LOGB>
+__global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* __restrict__ duals,
+                                                       long long nd, const float* __restrict__ isos,
+                                                       int n_iso, float* __restrict__ tris,
+                                                       const long long* __restrict__ seg_off, Scratch* sc,
+                                                       long long tile, const __grid_constant__ McConst mc) {
+  __shared__ McShared sh;
+  __shared__ float iso_sh[kMaxIso];
+  __shared__ long long off_sh[kMaxIso + 1];
+  __shared__ long long tile_base;
+  load_mc(sh, mc);
+  for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
+    iso_sh[k] = isos[k];
+    off_sh[k] = seg_off[k];
+  }
+  if (threadIdx.x == 0) off_sh[n_iso] = seg_off[n_iso];
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) tile_base = (long long)atomicAdd(&sc->tile, (unsigned long long)tile);
+    __syncthreads();
+    const long long t0 = tile_base;
+    __syncthreads();
+    if (t0 >= nd) break;
+    const long long t1 = min(nd, t0 + tile);
+    for (long long base = t0 + (threadIdx.x & ~31); base < t1; base += blockDim.x) {
+      const long long d = base + (threadIdx.x & 31);
+      unsigned v[8];
+      float sv[8];
+      float mn = 3.4e38f, mx = -3.4e38f;
+      const bool live = d < t1;
+      if (live) {
+        load_dual(duals, d, v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          sv[e] = __ldg(L.scal + v[e]);
+          mn = fminf(mn, sv[e]);
+          mx = fmaxf(mx, sv[e]);
+        }
+      }
+      for (int k = 0; k < n_iso; ++k) {
+        const float iso = iso_sh[k];
+        unsigned keep = 0;
+        int cas = 0;
+        if (live && mx > iso && !(mn > iso)) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) cas |= (sv[e] > iso ? 1 : 0) << e;
+          keep = kept_triangles(sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
+        }
+        if (__ballot_sync(kFull, keep != 0) == 0) continue;
+        const long long idx = warp_append(__popc(keep), &sc->n_tri[k]);
+        if (keep) {
+          const long long cap = off_sh[k + 1] - off_sh[k];
+          write_triangles<LOGB>(L, v, sv, iso, sh.packed[cas], keep, idx, cap, tris + 9 * off_sh[k],
+                                mc.edge_a, mc.edge_b);
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_get_duals(const uint4* __restrict__ duals, long long nd,
+                                                   const int* __restrict__ cell_id, int* __restrict__ out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nd; i += stride) {
+    const uint4 a = __ldg(duals + i);
+    reinterpret_cast<int4*>(out)[i] =
+        make_int4(__ldg(cell_id + a.x), __ldg(cell_id + a.y), __ldg(cell_id + a.z), __ldg(cell_id + a.w));
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launch wrappers
+// ---------------------------------------------------------------------------
+
+#define AMR_DISPATCH(logb, ...)            \
+  do {                                     \
+    if ((logb) == 2) {                     \
+      constexpr int LB = 2;                \
+      __VA_ARGS__;                         \
+    } else {                               \
+      constexpr int LB = 3;                \
+      __VA_ARGS__;                         \
+    }                                      \
+  } while (0)
+
+cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
+                                 long long n, unsigned long long* hkeys, int* hvals,
+                                 unsigned long long hmask, int4* bricks, Scratch* sc, int grid,
+                                 int block, cudaStream_t st) {
+  AMR_DISPATCH(logb, (k_insert_bricks<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, hkeys, hvals, hmask,
+                                                                   bricks, sc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* lvl, const float* s,
+                                 long long n, Locator loc, int* cell_id, float* scal, Scratch* sc,
+                                 int grid, int block, cudaStream_t st) {
+  AMR_DISPATCH(logb, (k_scatter_cells<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, loc, cell_id, scal, sc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, long long n_slots,
+                                 int check_overlap, Scratch* sc, int grid, int block,
+                                 cudaStream_t st) {
+  AMR_DISPATCH(logb, (k_resolve_views<LB><<<grid, block, 0, st>>>(loc, view, n_slots, check_overlap, sc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dual_cells(int logb, Locator loc, long long n_bricks, uint4* duals, long long cap,
+                              Scratch* sc, cudaStream_t st) {
+  if (n_bricks <= 0) return cudaSuccess;
+  const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
+  AMR_DISPATCH(logb, (k_dual_cells<LB><<<grid, 1 << (3 * LB), 0, st>>>(loc, n_bricks, duals, cap, sc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, float iso, float* tris,
+                      long long cap, unsigned long long* counter, unsigned char* cases,
+                      unsigned char* ntri, const McConst& mc, int grid, cudaStream_t st) {
+  if (nd <= 0) return cudaSuccess;
+  if (cases || ntri) {
+    AMR_DISPATCH(logb, (k_mc<LB, false, true><<<grid, 256, 0, st>>>(loc, duals, nd, iso, tris, cap, counter,
+                                                                     cases, ntri, mc)));
+  } else {
+    AMR_DISPATCH(logb, (k_mc<LB, true, false><<<grid, 256, 0, st>>>(loc, duals, nd, iso, tris, cap, counter,
+                                                                     cases, ntri, mc)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mc_batch_count(int logb, Locator loc, const uint4* duals, long long nd,
+                                  const float* isos, int n_iso, Scratch* sc, const McConst& mc,
+                                  int grid, cudaStream_t st) {
+  if (nd <= 0) return cudaSuccess;
+  AMR_DISPATCH(logb, (k_mc_batch_count<LB><<<grid, 256, 0, st>>>(loc, duals, nd, isos, n_iso, sc, mc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long long nd,
+                                 const float* isos, int n_iso, float* tris, const long long* seg_off,
+                                 Scratch* sc, const McConst& mc, int grid, long long tile,
+                                 cudaStream_t st) {
+  if (nd <= 0) return cudaSuccess;
+  AMR_DISPATCH(logb, (k_mc_batch_emit<LB><<<grid, 256, 0, st>>>(loc, duals, nd, isos, n_iso, tris, seg_off,
+                                                                 sc, tile, mc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_duals(const uint4* duals, long long nd, const int* cell_id, int* out, int grid,
+                             cudaStream_t st) {
+  if (nd <= 0) return cudaSuccess;
+  k_get_duals<<<grid, 256, 0, st>>>(duals, nd, cell_id, out);
+  return cudaGetLastError();
+}
+
+}  // namespace amriso

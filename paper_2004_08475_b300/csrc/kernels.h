@@ -1,0 +1,93 @@
+// Declarations shared by the CUDA kernels (kernels.cu) and the C ABI
+// (api.cu). Nothing here is part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace amriso {
+
+constexpr uint32_t kReject = 0xFFFFFFFFu;          // "does not exist" in a view
+constexpr unsigned long long kEmptyKey = ~0ull;     // free hash slot
+constexpr int kMaxLevel = 14;                       // levels 0..14
+constexpr int kMaxIso = 64;                         // iso-values per batch
+
+enum ErrBits : uint32_t {
+  ERR_UNALIGNED = 1u,
+  ERR_RANGE = 2u,
+  ERR_NONFINITE = 4u,
+  ERR_DUPLICATE = 8u,
+  ERR_OVERLAP = 16u,
+  ERR_HASH_FULL = 32u,
+  ERR_TIMEOUT = 64u,
+};
+
+// Small device-resident counters, one allocation per context.
+struct Scratch {
+  unsigned long long n_bricks;
+  unsigned long long n_dual;
+  unsigned long long tile;              // persistent-kernel work counter
+  unsigned long long n_tri[kMaxIso];    // per iso-value triangle counters
+  unsigned int err;
+  int lo[3];                            // bounding box: min lower corner
+  int hi[3];                            // max (lower corner + width)
+  int max_level;
+};
+
+// Device view of the point-location structure (Sec. 3.2).
+struct Locator {
+  const unsigned long long* hkeys;  // [hcap] brick keys (level, brick coords)
+  const int* hvals;                 // [hcap] brick index
+  unsigned long long hmask;         // hcap - 1 (hcap a power of two)
+  const int4* bricks;               // [n_bricks] origin x,y,z (finest units), level
+  const int* cell_id;               // [n_slots] input index of the slot's cell or -1
+  const float* scal;                // [n_slots] scalar of the slot's cell
+  const unsigned* view;             // [n_slots] resolved cell slot, or kReject
+  int levels;                       // max level + 1
+};
+
+// Marching Cubes table in the form the kernels read (generated on the host).
+struct McConst {
+  unsigned long long packed[256];   // 4-bit edge ids, 3 per triangle
+  unsigned char count[256];         // triangles per case
+  unsigned long long edge_a;        // 4-bit lower corner of edge k at bits 4k
+  unsigned long long edge_b;        // 4-bit upper corner of edge k
+};
+
+// ---- launches (all asynchronous on `st`) --------------------------------
+// Each returns the launch's cudaError_t (cudaGetLastError after launch).
+
+cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
+                                 long long n, unsigned long long* hkeys, int* hvals,
+                                 unsigned long long hmask, int4* bricks, Scratch* sc,
+                                 int grid, int block, cudaStream_t st);
+
+cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* lvl, const float* s,
+                                 long long n, Locator loc, int* cell_id, float* scal, Scratch* sc,
+                                 int grid, int block, cudaStream_t st);
+
+cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, long long n_slots,
+                                 int check_overlap, Scratch* sc, int grid, int block,
+                                 cudaStream_t st);
+
+cudaError_t launch_dual_cells(int logb, Locator loc, long long n_bricks, uint4* duals,
+                              long long cap, Scratch* sc, cudaStream_t st);
+
+cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, float iso,
+                      float* tris, long long cap, unsigned long long* counter,
+                      unsigned char* cases, unsigned char* ntri, const McConst& mc, int grid,
+                      cudaStream_t st);
+
+cudaError_t launch_mc_batch_count(int logb, Locator loc, const uint4* duals, long long nd,
+                                  const float* isos, int n_iso, Scratch* sc, const McConst& mc,
+                                  int grid, cudaStream_t st);
+
+cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long long nd,
+                                 const float* isos, int n_iso, float* tris,
+                                 const long long* seg_off, Scratch* sc, const McConst& mc,
+                                 int grid, long long tile, cudaStream_t st);
+
+cudaError_t launch_get_duals(const uint4* duals, long long nd, const int* cell_id, int* out,
+                             int grid, cudaStream_t st);
+
+}  // namespace amriso

@@ -1,0 +1,203 @@
+"""CUDA path vs oracle, element by element: bit-exact dual cells (sorted
+8-tuples of cell IDs), case indices and per-dual triangle counts; triangle
+vertices within 1e-5 of the domain extent after canonical ordering (the
+kernels use the oracle's fp32 operation order, so they are expected to be
+bit-exact)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2004_08475_b300 import synth
+from tests.parity import canonical, compare, owners_of, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _extent(info):
+    return float(max(info["domain"]))
+
+
+@pytest.mark.parametrize("logb", [2, 3])
+def test_sphere_tiny(logb):
+    xyz, lv, s, iso, info = synth.sphere_tiny()
+    g = run_gpu(xyz, lv, s, iso, log2_brick=logb)
+    o = run_oracle(xyz, lv, s, iso)
+    r = compare(g, o, _extent(info))
+    assert r["duals"] == 5827
+    assert r["bit_exact_frac"] == 1.0
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_octrees(seed):
+    levels = 2 + seed % 4
+    gen = synth.random_octree(seed, levels=levels, roots=5 if levels < 5 else 3, p_split=0.45,
+                              p_hole=0.0 if seed % 3 == 0 else 0.08,
+                              field="random" if seed % 2 else "sphere")
+    xyz, lv, s, iso, info = gen
+    g = run_gpu(xyz, lv, s, iso, log2_brick=2 + seed % 2)
+    o = run_oracle(xyz, lv, s, iso)
+    compare(g, o, _extent(info))
+
+
+@pytest.mark.parametrize("n,l,origin", [(2, 0, (0, 0, 0)), (9, 0, (-5, 3, 17)), (12, 3, (-64, 0, 8)),
+                                         (17, 1, (1000, -2000, 30))])
+def test_uniform_grid(n, l, origin):
+    xyz, lv, s, iso, info = synth.uniform_grid(n, l, origin)
+    g = run_gpu(xyz, lv, s, iso)
+    assert g["nd"] == (n - 1) ** 3
+    o = run_oracle(xyz, lv, s, iso)
+    compare(g, o, float(n << l))
+
+
+def test_octree_gaussians_small():
+    gen = synth.octree_gaussians(seed=12, roots=6, root_level=4)
+    xyz, lv, s, iso, info = gen
+    assert info["n"] > 10000
+    for logb in (2, 3):
+        g = run_gpu(xyz, lv, s, iso, log2_brick=logb)
+        o = run_oracle(xyz, lv, s, iso)
+        compare(g, o, _extent(info))
+
+
+def test_block_vortex_small():
+    gen = synth.block_vortex(seed=13, dims=(4, 2, 2), scale=0.12, tau=0.004, iso=0.05)
+    xyz, lv, s, iso, info = gen
+    assert info["n"] > 10000
+    g = run_gpu(xyz, lv, s, iso)
+    o = run_oracle(xyz, lv, s, iso)
+    compare(g, o, _extent(info))
+
+
+def test_wing_small():
+    gen = synth.wing_bands(seed=14, dims=(24, 24, 8), bands=(3.0, 7.0, 14.0), iso=8.0)
+    xyz, lv, s, iso, info = gen
+    assert info["n"] > 10000
+    g = run_gpu(xyz, lv, s, iso)
+    o = run_oracle(xyz, lv, s, iso)
+    compare(g, o, _extent(info))
+
+
+def test_host_pointer_upload():
+    xyz, lv, s, iso, info = synth.random_octree(77, levels=4, roots=4, p_hole=0.05)
+    g = run_gpu(xyz, lv, s, iso, host_upload=True)
+    o = run_oracle(xyz, lv, s, iso)
+    compare(g, o, _extent(info))
+
+
+def test_empty_and_single():
+    from paper_2004_08475_b300 import amriso
+    ctx = amriso.AmrContext()
+    ctx.upload(torch.zeros((0, 3), dtype=torch.int32, device="cuda"),
+               torch.zeros(0, dtype=torch.uint8, device="cuda"),
+               torch.zeros(0, dtype=torch.float32, device="cuda"))
+    ctx.build_locator()
+    assert ctx.dual_cells() == 0
+    assert ctx.iso(0.5).shape[0] == 0
+    ctx.upload(torch.tensor([[4, 8, -12]], dtype=torch.int32, device="cuda"),
+               torch.tensor([2], dtype=torch.uint8, device="cuda"),
+               torch.tensor([1.0], device="cuda"))
+    ctx.build_locator()
+    assert ctx.dual_cells() == 0
+
+
+def test_deep_jumps_collapsed_duals():
+    """Five levels on a 2^3 root grid with heavy splitting: transition duals
+    with many repeated vertices and level jumps up to 4."""
+    for seed in range(4):
+        gen = synth.random_octree(100 + seed, levels=5, roots=2, p_split=0.7, p_hole=0.0,
+                                  field="random")
+        xyz, lv, s, iso, info = gen
+        g = run_gpu(xyz, lv, s, iso, log2_brick=2)
+        o = run_oracle(xyz, lv, s, iso)
+        compare(g, o, _extent(info))
+
+
+@pytest.mark.parametrize("what", ["duplicate", "unaligned", "nonfinite", "level", "overlap", "extent"])
+def test_invalid_input_codes(what):
+    from paper_2004_08475_b300 import amriso
+    xyz = torch.tensor([[0, 0, 0], [2, 0, 0], [4, 0, 0]], dtype=torch.int32)
+    lv = torch.tensor([1, 1, 1], dtype=torch.uint8)
+    s = torch.tensor([0.0, 1.0, 2.0])
+    overlap = False
+    want = {"duplicate": amriso.ERR_DUPLICATE, "unaligned": amriso.ERR_UNALIGNED,
+            "nonfinite": amriso.ERR_NONFINITE, "level": amriso.ERR_RANGE,
+            "overlap": amriso.ERR_OVERLAP, "extent": amriso.ERR_RANGE}[what]
+    if what == "duplicate":
+        xyz[2] = xyz[1]
+    elif what == "unaligned":
+        xyz[1, 0] = 3
+    elif what == "nonfinite":
+        s[2] = float("nan")
+    elif what == "level":
+        lv[0] = 15
+    elif what == "overlap":
+        xyz[2] = torch.tensor([2, 0, 0])
+        lv[2] = 0
+        overlap = True
+    elif what == "extent":
+        xyz[2, 1] = 1 << 22
+    ctx = amriso.AmrContext()
+    ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+    with pytest.raises(amriso.AmrError) as e:
+        ctx.build_locator(check_overlap=overlap)
+    assert e.value.code == want
+    with pytest.raises(amriso.AmrError) as e:
+        ctx.dual_cells()
+    assert e.value.code == amriso.ERR_STATE
+
+
+def test_capacity_and_exact_count():
+    from paper_2004_08475_b300 import amriso
+    xyz, lv, s, iso, info = synth.sphere_tiny()
+    ctx = amriso.AmrContext()
+    ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+    ctx.build_locator()
+    ctx.dual_cells()
+    full = ctx.iso(iso)
+    small = torch.empty((10, 3, 3), dtype=torch.float32, device="cuda")
+    n = ctx.iso_count(iso, small)
+    assert n == full.shape[0] > 10
+    host = torch.empty((n, 3, 3), dtype=torch.float32).pin_memory()
+    assert ctx.iso_count(iso, host) == n
+    assert (canonical(host.numpy()) == canonical(full.cpu().numpy())).all()
+
+
+def test_iso_batch_equals_single():
+    from paper_2004_08475_b300 import amriso
+    gen = synth.octree_gaussians(seed=21, roots=5, root_level=4)
+    xyz, lv, s, iso, info = gen
+    ctx = amriso.AmrContext()
+    ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+    ctx.build_locator()
+    ctx.dual_cells()
+    isos = [iso * (0.5 + 0.1 * k) for k in range(12)]
+    tris, offs = ctx.iso_batch(isos)
+    for k, v in enumerate(isos):
+        one = ctx.iso(v).cpu().numpy()
+        seg = tris[offs[k]:offs[k + 1]].cpu().numpy()
+        assert seg.shape == one.shape
+        assert (canonical(seg) == canonical(one)).all()
+
+
+def test_octree_full_size_sampled():
+    """The 10M-cell octree at full size: every dual owned by a sample of
+    cells equals the oracle's, with equal case and triangle counts; the
+    totals are consistent."""
+    import oracle
+    gen = synth.octree_gaussians(device="cuda")
+    xyz, lv, s, iso, info = gen
+    assert 9_000_000 < info["n"] < 11_000_000
+    g = run_gpu(xyz, lv, s, iso)
+    assert int(g["ntri"].sum()) == g["tris"].shape[0]
+    x, l, v = xyz.cpu().numpy(), lv.cpu().numpy(), s.cpu().numpy()
+    rng = np.random.default_rng(5)
+    sample = rng.choice(x.shape[0], size=3000, replace=False)
+    m = oracle.OracleMesh(x, l)
+    od = m.duals(owners=sample)
+    r = m.iso(v, od, iso, want_keys=False)
+    gown = owners_of(g["duals"], x, l)
+    sel = np.isin(gown, sample)
+    o = {"duals": od, "cases": r["cases"], "ntri": r["ntri"], "tris": r["tris"]}
+    gs = {"duals": g["duals"][sel], "cases": g["cases"][sel], "ntri": g["ntri"][sel],
+          "tris": r["tris"]}
+    compare(gs, o, _extent(info))
