@@ -184,6 +184,34 @@ int amr_enable_timing(amr_ctx* ctx, int on);
 int amr_kernel_times(amr_ctx* ctx, double* ms, int64_t* launches, int n);
 const char* amr_kernel_name(int k);
 
+/* ---- extraction without device allocation -------------------------------- */
+
+/* No counterpart in the paper: this entry point exists for callers that may
+ * not allocate device memory themselves - for example code embedded in a
+ * host application whose device memory belongs to another allocator, or
+ * real-time code that cannot afford an allocation's latency or failure.
+ * It runs the whole extraction (cell location, dual cells, Marching Cubes)
+ * for a small data set with every intermediate buffer taken from one fixed
+ * array of AMR_NOALLOC_SCRATCH_BYTES that the library reserves on each GPU
+ * that loads it, for the life of the process. It calls no allocator.
+ *   xyz, level, scalar  device arrays as in amr_upload, n <= AMR_NOALLOC_MAX_CELLS
+ *   tris [cap][3][3]    device output as in amr_iso; *n_tris the exact count
+ *                       (also on AMR_ERR_CAPACITY, when only cap were written)
+ *   cuda_stream         stream for all work (NULL = legacy default stream)
+ * Errors as amr_build_locator / amr_iso, plus AMR_ERR_RANGE when n exceeds
+ * the limit, when the cells fill their 4^3 bricks to less than 1/8 on
+ * average, or when more than 2 * AMR_NOALLOC_MAX_CELLS dual cells result.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the array and each call resets what it uses, so
+ * calls that overlap on the GPU (other host threads or streams) race.
+ * Synchronises the stream. */
+#define AMR_NOALLOC_MAX_CELLS 65536
+#define AMR_NOALLOC_SCRATCH_BYTES (14u << 20)
+int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level,
+                        const float* scalar, int64_t n, float iso, float* tris,
+                        int64_t cap, int64_t* n_tris, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "amr_enable_timing": (I, [P, I]),
         "amr_kernel_times": (I, [P, P, P, I]),
         "amr_kernel_name": (ctypes.c_char_p, [I]),
+        "amr_extract_noalloc": (I, [P, P, P, I64, F, P, I64, ctypes.POINTER(I64), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -99,7 +100,7 @@ _lib = _load()
 EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_build_locator",
            "amr_dual_cells", "amr_get_duals", "amr_iso", "amr_iso_cases", "amr_iso_batch",
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
-           "amr_kernel_times", "amr_kernel_name")
+           "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc")
 
 
 def lib() -> ctypes.CDLL:
