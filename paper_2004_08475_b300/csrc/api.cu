@@ -23,11 +23,11 @@ struct DevBuf {
 
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
-  KT_GET_DUALS, KT_COUNT
+  KT_GET_DUALS, KT_NEIGHBORS, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
-    "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals"};
+    "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -72,7 +72,7 @@ struct amr_ctx {
   float alpha = 0.5f;
   int block = 256;
   int check_overlap = 0;
-  DevBuf hkeys, hvals, bricks, cell_id, scal, view;
+  DevBuf hkeys, hvals, bricks, cell_id, scal, view, nbr;
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
   int levels = 0;
@@ -286,7 +286,7 @@ void amr_destroy(amr_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                    &c->cell_id, &c->scal, &c->view, &c->duals, &c->scratch, &c->stage_buf,
+                    &c->cell_id, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch, &c->stage_buf,
                     &c->iso_buf, &c->seg_buf};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
@@ -420,6 +420,12 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
                                     dev_sc(c), grid_for(c, c->n_slots, block, 2048 / block), block,
                                     c->stream));
     }
+    AMR_TRY(ensure(c->nbr, (size_t)c->n_bricks * 27 * 4));
+    {
+      KernelTimer kt(c, KT_NEIGHBORS);
+      AMR_CUDA(launch_brick_neighbors(logb, L, c->n_bricks, static_cast<int*>(c->nbr.p),
+                                      grid_for(c, c->n_bricks * 27, 256, 8), c->stream));
+    }
     AMR_TRY(read_scratch(c));
     const int rc = err_code(c->host_sc->err);
     if (rc != AMR_OK) return rc;
@@ -439,8 +445,8 @@ int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
     AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->n_dual, 0, sizeof(unsigned long long), c->stream));
     {
       KernelTimer kt(c, KT_DUAL);
-      AMR_CUDA(launch_dual_cells(c->logb, make_locator(c), c->n_bricks, static_cast<uint4*>(c->duals.p),
-                                 c->dual_cap, dev_sc(c), c->stream));
+      AMR_CUDA(launch_dual_cells(c->logb, make_locator(c), static_cast<const int*>(c->nbr.p), c->n_bricks,
+                                 static_cast<uint4*>(c->duals.p), c->dual_cap, dev_sc(c), c->stream));
     }
     AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_dual, &dev_sc(c)->n_dual, sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, c->stream));
@@ -590,8 +596,8 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->n_levels = c->stage >= 2 ? c->levels : 0;
   info->log2_brick = c->logb;
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                          &c->cell_id, &c->scal, &c->view, &c->duals, &c->scratch, &c->stage_buf,
-                          &c->iso_buf, &c->seg_buf};
+                          &c->cell_id, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch,
+                          &c->stage_buf, &c->iso_buf, &c->seg_buf};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);
   info->device_bytes = total;

@@ -286,6 +286,39 @@ __global__ void __launch_bounds__(1024) k_resolve_views(Locator L, unsigned* vie
   if (err) atomicOr(&sc->err, err);
 }
 
+// Pass over (brick, neighbour) pairs: for every brick its 26 neighbouring
+// brick regions (and itself) resolved once - the same-level brick there, or
+// the first coarser brick covering that region, or none. An aligned level-l
+// brick region lies inside exactly one brick region of each coarser level,
+// so one brick answers for the whole neighbour region. Value: brick index |
+// level << 27, or -1.
+template <int LOGB>
+__global__ void __launch_bounds__(256) k_brick_neighbors(Locator L, long long n_bricks,
+                                                         int* __restrict__ nbr) {
+  constexpr int B = 1 << LOGB;
+  const long long total = n_bricks * 27;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const long long bi = i / 27;
+    const int t = (int)(i - bi * 27);
+    const int4 b = __ldg(L.bricks + bi);
+    const int l = b.w;
+    int out = -1;
+    if (t == 13) {
+      out = (int)bi | (l << 27);
+    } else {
+      const int ext = B << l;
+      const int qx = b.x + (t % 3 - 1) * ext, qy = b.y + ((t / 3) % 3 - 1) * ext,
+                qz = b.z + (t / 9 - 1) * ext;
+      for (int lv = l; lv < L.levels; ++lv) {
+        const int bj = find_brick(L, brick_key<LOGB>(qx, qy, qz, lv));
+        if (bj >= 0) { out = bj | (lv << 27); break; }
+      }
+    }
+    nbr[i] = out;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Dual cells (Sec. 4.2 - 4.4)
 // ---------------------------------------------------------------------------
@@ -328,7 +361,8 @@ __constant__ DualMasks c_masks = make_dual_masks();
 // with one atomic per CTA.
 template <int LOGB>
 __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
-    Locator L, long long n_bricks, uint4* __restrict__ duals, long long cap, Scratch* sc) {
+    Locator L, const int* __restrict__ nbr, long long n_bricks, uint4* __restrict__ duals, long long cap,
+    Scratch* sc) {
   constexpr int B = 1 << LOGB;
   constexpr int R = B + 2;
   constexpr int NT = B * B * B;
@@ -336,43 +370,35 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
   constexpr int NW = (NT + 31) / 32;
   __shared__ unsigned rv[NR];
   __shared__ unsigned char rs[NR];
-  __shared__ int nb_bi[27];
-  __shared__ int nb_lv[27];
+  __shared__ int nb[27];
   __shared__ unsigned wsum[NW];
   __shared__ unsigned long long cta_base;
   const int t = threadIdx.x;
   const int lane = t & 31, wp = t >> 5;
   const int px = compact<LOGB>(t), py = compact<LOGB>(t >> 1), pz = compact<LOGB>(t >> 2);
   const int c0 = px + R * (py + R * pz);   // neighbourhood origin (cell - 1) in the region
+  const int cself = c0 + 1 + R + R * R;    // this thread's own cell in the region
   for (long long bi = blockIdx.x; bi < n_bricks; bi += gridDim.x) {
     const int4 b = __ldg(L.bricks + bi);
     const int l = b.w;
-    if (t < 27) {
-      int fb = -1, fl = l;
-      if (t == 13) {
-        fb = (int)bi;
-      } else {
-        const int ext = B << l;
-        const int qx = b.x + (t % 3 - 1) * ext, qy = b.y + ((t / 3) % 3 - 1) * ext,
-                  qz = b.z + (t / 9 - 1) * ext;
-        for (int lv = l; lv < L.levels; ++lv) {
-          const int bj = find_brick(L, brick_key<LOGB>(qx, qy, qz, lv));
-          if (bj >= 0) { fb = bj; fl = lv; break; }
-        }
-      }
-      nb_bi[t] = fb;
-      nb_lv[t] = fl;
+    if (t < 27) nb[t] = __ldg(nbr + bi * 27 + t);
+    {   // the brick itself: one coalesced read, slot t is this thread's cell
+      const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)t;
+      const unsigned v = __ldg(L.view + s2);
+      rv[cself] = v;
+      rs[cself] = v == s2;
     }
     __syncthreads();
-    for (int r = t; r < NR; r += NT) {
+    for (int r = t; r < NR; r += NT) {   // the one-cell halo
       const int rx = r % R, ry = (r / R) % R, rz = r / (R * R);
+      if (rx >= 1 && rx <= B && ry >= 1 && ry <= B && rz >= 1 && rz <= B) continue;
       const int nbi = (rx == 0 ? 0 : (rx == R - 1 ? 2 : 1)) + 3 * (ry == 0 ? 0 : (ry == R - 1 ? 2 : 1)) +
                       9 * (rz == 0 ? 0 : (rz == R - 1 ? 2 : 1));
-      const int fb = nb_bi[nbi];
+      const int e = nb[nbi];
       unsigned v = kReject;
       unsigned char same = 0;
-      if (fb >= 0) {
-        const int lv = nb_lv[nbi];
+      if (e >= 0) {
+        const int fb = e & ((1 << 27) - 1), lv = e >> 27;
         const int x = b.x + ((rx - 1) << l), y = b.y + ((ry - 1) << l), z = b.z + ((rz - 1) << l);
         const unsigned s2 = ((unsigned)fb << (3 * LOGB)) | local_index<LOGB>(x, y, z, lv);
         v = __ldg(L.view + s2);
@@ -383,7 +409,7 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
     }
     __syncthreads();
     unsigned emit = 0;
-    if (rs[c0 + 1 + R + R * R]) {   // this slot holds an actual level-l cell
+    if (rs[cself]) {   // this slot holds an actual level-l cell
       unsigned exist = 0, samem = 0;
 #pragma unroll
       for (int o = 0; o < 27; ++o) {
@@ -459,10 +485,18 @@ __device__ __forceinline__ void load_dual(const uint4* __restrict__ duals, long 
   v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
 }
 
+// v[i] for a run-time i without moving v to local memory.
+__device__ __forceinline__ unsigned sel8(const unsigned v[8], int i) {
+  unsigned r = v[0];
+#pragma unroll
+  for (int e = 1; e < 8; ++e) r = (i == e) ? v[e] : r;
+  return r;
+}
+
 // Edge key (unordered pair of cells) of hexahedron edge k.
 __device__ __forceinline__ unsigned long long edge_key(const unsigned v[8], int k,
                                                        unsigned long long ea, unsigned long long eb) {
-  const unsigned a = v[(ea >> (4 * k)) & 15], b = v[(eb >> (4 * k)) & 15];
+  const unsigned a = sel8(v, (int)((ea >> (4 * k)) & 15)), b = sel8(v, (int)((eb >> (4 * k)) & 15));
   return a < b ? ((unsigned long long)a << 32) | b : ((unsigned long long)b << 32) | a;
 }
 
@@ -525,14 +559,15 @@ __device__ __forceinline__ long long warp_append(unsigned k, unsigned long long*
   return (long long)base + incl - k;
 }
 
+// Writes the kept triangles of one dual. The dual's 8 vertex slots and
+// scalars sit in this thread's shared-memory row (indexed by table-driven
+// corner numbers, which registers cannot be).
 template <int LOGB>
-__device__ __forceinline__ void write_triangles(const Locator& L, const unsigned v[8], const float sv[8],
-                                                float iso, unsigned long long packed, unsigned keep,
-                                                long long idx, long long cap, float* __restrict__ tris,
-                                                unsigned long long ea, unsigned long long eb) {
-  int4 p[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) p[e] = slot_cell<LOGB>(L.bricks, v[e]);
+__device__ __forceinline__ void write_triangles(const int4* __restrict__ bricks, const unsigned* vr,
+                                                const float* sr, float iso, unsigned long long packed,
+                                                unsigned keep, long long idx, long long cap,
+                                                float* __restrict__ tris, unsigned long long ea,
+                                                unsigned long long eb) {
   for (int t = 0; t < 5; ++t) {
     if (!((keep >> t) & 1u)) continue;
     if (idx < cap) {
@@ -541,7 +576,8 @@ __device__ __forceinline__ void write_triangles(const Locator& L, const unsigned
       for (int c = 0; c < 3; ++c) {
         const int k = (int)((packed >> (12 * t + 4 * c)) & 15);
         const int a = (int)((ea >> (4 * k)) & 15), b = (int)((eb >> (4 * k)) & 15);
-        const float3 q = edge_vertex(p[a], sv[a], p[b], sv[b], iso);
+        const float3 q = edge_vertex(slot_cell<LOGB>(bricks, vr[a]), sr[a], slot_cell<LOGB>(bricks, vr[b]),
+                                     sr[b], iso);
         out[3 * c + 0] = q.x;
         out[3 * c + 1] = q.y;
         out[3 * c + 2] = q.z;
@@ -551,46 +587,82 @@ __device__ __forceinline__ void write_triangles(const Locator& L, const unsigned
   }
 }
 
-// One thread per dual cell: gather the 8 vertex scalars, build the case
-// index (bit e set iff s_e > iso), keep the case's triangles that have three
-// different edge keys, append them with one atomic per warp and write their
-// interpolated vertices. Optionally writes per-dual case and triangle count.
+constexpr int kRow = 9;   // shared-memory row stride (words): conflict-free across a warp
+
+__device__ __forceinline__ void stage_row(unsigned* vr, float* sr, const unsigned v[8], const float sv[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    vr[e] = v[e];
+    sr[e] = sv[e];
+  }
+}
+
+__device__ __forceinline__ int case_of(const unsigned v[8], float sv[8], const float* __restrict__ scal,
+                                       float iso) {
+  int cas = 0;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    sv[e] = __ldg(scal + v[e]);
+    cas |= (sv[e] > iso ? 1 : 0) << e;
+  }
+  return cas;
+}
+
+// One lane per dual, two duals per lane per step: gather the 8 vertex
+// scalars, build the case index (bit e set iff s_e > iso), keep the case's
+// triangles that have three different edge keys, append them with one
+// atomic per warp and write their interpolated vertices. Optionally writes
+// per-dual case and triangle count instead.
 template <int LOGB, bool EMIT, bool CASES>
 __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
                                             float iso, float* __restrict__ tris, long long cap,
                                             unsigned long long* counter, unsigned char* cases,
                                             unsigned char* ntri, const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
+  __shared__ unsigned row_v[EMIT ? 256 * kRow : 1];
+  __shared__ float row_s[EMIT ? 256 * kRow : 1];
   load_mc(sh, mc);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (long long base = wid * 32; base < nd; base += nwarps * 32) {
-    const long long d = base + lane;
-    unsigned v[8];
-    float sv[8];
-    int cas = 0;
-    unsigned keep = 0;
-    if (d < nd) {
-      load_dual(duals, d, v);
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        sv[e] = __ldg(L.scal + v[e]);
-        cas |= (sv[e] > iso ? 1 : 0) << e;
+  unsigned* vr = row_v + (EMIT ? threadIdx.x * kRow : 0);
+  float* sr = row_s + (EMIT ? threadIdx.x * kRow : 0);
+  for (long long base = wid * 64; base < nd; base += nwarps * 64) {
+    const long long d0 = base + lane, d1 = base + 32 + lane;
+    const bool a0 = d0 < nd, a1 = d1 < nd;
+    unsigned v0[8], v1[8];
+    float s0[8], s1[8];
+    if (a0) load_dual(duals, d0, v0);
+    if (a1) load_dual(duals, d1, v1);
+    int c0 = 0, c1 = 0;
+    if (a0) c0 = case_of(v0, s0, L.scal, iso);
+    if (a1) c1 = case_of(v1, s1, L.scal, iso);
+    unsigned k0 = 0, k1 = 0;
+    if (a0 && sh.count[c0]) k0 = kept_triangles(sh.packed[c0], sh.count[c0], v0, mc.edge_a, mc.edge_b);
+    if (a1 && sh.count[c1]) k1 = kept_triangles(sh.packed[c1], sh.count[c1], v1, mc.edge_a, mc.edge_b);
+    if (CASES) {
+      if (a0) {
+        if (cases) cases[d0] = (unsigned char)c0;
+        if (ntri) ntri[d0] = (unsigned char)__popc(k0);
       }
-      const int cnt = sh.count[cas];
-      if (cnt) keep = kept_triangles(sh.packed[cas], cnt, v, mc.edge_a, mc.edge_b);
-      if (CASES) {
-        if (cases) cases[d] = (unsigned char)cas;
-        if (ntri) ntri[d] = (unsigned char)__popc(keep);
+      if (a1) {
+        if (cases) cases[d1] = (unsigned char)c1;
+        if (ntri) ntri[d1] = (unsigned char)__popc(k1);
       }
     }
     if (EMIT) {
-      if (__ballot_sync(kFull, keep != 0) == 0) continue;
-      const long long idx = warp_append(__popc(keep), counter);
-      if (keep)
-        write_triangles<LOGB>(L, v, sv, iso, sh.packed[cas], keep, idx, cap, tris, mc.edge_a, mc.edge_b);
+      if (__ballot_sync(kFull, (k0 | k1) != 0) == 0) continue;
+      long long idx = warp_append(__popc(k0) + __popc(k1), counter);
+      if (k0) {
+        stage_row(vr, sr, v0, s0);
+        write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c0], k0, idx, cap, tris, mc.edge_a, mc.edge_b);
+        idx += __popc(k0);
+      }
+      if (k1) {
+        stage_row(vr, sr, v1, s1);
+        write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c1], k1, idx, cap, tris, mc.edge_a, mc.edge_b);
+      }
     }
   }
 }
@@ -652,6 +724,10 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
   __shared__ float iso_sh[kMaxIso];
   __shared__ long long off_sh[kMaxIso + 1];
   __shared__ long long tile_base;
+  __shared__ unsigned row_v[256 * kRow];
+  __shared__ float row_s[256 * kRow];
+  unsigned* vr = row_v + threadIdx.x * kRow;
+  float* sr = row_s + threadIdx.x * kRow;
   load_mc(sh, mc);
   for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
     iso_sh[k] = isos[k];
@@ -694,7 +770,8 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
         const long long idx = warp_append(__popc(keep), &sc->n_tri[k]);
         if (keep) {
           const long long cap = off_sh[k + 1] - off_sh[k];
-          write_triangles<LOGB>(L, v, sv, iso, sh.packed[cas], keep, idx, cap, tris + 9 * off_sh[k],
+          stage_row(vr, sr, v, sv);
+          write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[cas], keep, idx, cap, tris + 9 * off_sh[k],
                                 mc.edge_a, mc.edge_b);
         }
       }
@@ -752,11 +829,18 @@ cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, long lon
   return cudaGetLastError();
 }
 
-cudaError_t launch_dual_cells(int logb, Locator loc, long long n_bricks, uint4* duals, long long cap,
-                              Scratch* sc, cudaStream_t st) {
+cudaError_t launch_brick_neighbors(int logb, Locator loc, long long n_bricks, int* nbr, int grid,
+                                   cudaStream_t st) {
+  if (n_bricks <= 0) return cudaSuccess;
+  AMR_DISPATCH(logb, (k_brick_neighbors<LB><<<grid, 256, 0, st>>>(loc, n_bricks, nbr)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, long long n_bricks, uint4* duals,
+                              long long cap, Scratch* sc, cudaStream_t st) {
   if (n_bricks <= 0) return cudaSuccess;
   const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
-  AMR_DISPATCH(logb, (k_dual_cells<LB><<<grid, 1 << (3 * LB), 0, st>>>(loc, n_bricks, duals, cap, sc)));
+  AMR_DISPATCH(logb, (k_dual_cells<LB><<<grid, 1 << (3 * LB), 0, st>>>(loc, nbr, n_bricks, duals, cap, sc)));
   return cudaGetLastError();
 }
 

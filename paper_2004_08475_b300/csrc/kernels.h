@@ -70,7 +70,11 @@ cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, long lon
                                  int check_overlap, Scratch* sc, int grid, int block,
                                  cudaStream_t st);
 
-cudaError_t launch_dual_cells(int logb, Locator loc, long long n_bricks, uint4* duals,
+// nbr[n_bricks][27]: neighbour brick | level << 27, or -1 (see kernels.cu)
+cudaError_t launch_brick_neighbors(int logb, Locator loc, long long n_bricks, int* nbr, int grid,
+                                   cudaStream_t st);
+
+cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, long long n_bricks, uint4* duals,
                               long long cap, Scratch* sc, cudaStream_t st);
 
 cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, float iso,

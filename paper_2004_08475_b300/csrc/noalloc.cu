@@ -38,11 +38,13 @@ constexpr size_t kOffScratch = 0;
 constexpr size_t kOffKeys = align256(kOffScratch + sizeof(Scratch));
 constexpr size_t kOffVals = align256(kOffKeys + kHashCap * 8);
 constexpr size_t kOffBricks = align256(kOffVals + kHashCap * 4);
-constexpr size_t kOffCellId = align256(kOffBricks + kHashCap * 16);
+constexpr size_t kOffCellId = align256(kOffBricks + kMaxCells * 16);   // a brick holds >= 1 cell
 constexpr size_t kOffScal = align256(kOffCellId + kMaxSlots * 4);
 constexpr size_t kOffView = align256(kOffScal + kMaxSlots * 4);
 constexpr size_t kOffDuals = align256(kOffView + kMaxSlots * 4);
-constexpr size_t kScratchBytes = align256(kOffDuals + kMaxDuals * 32);
+constexpr size_t kOffNbr = align256(kOffDuals + kMaxDuals * 32);
+constexpr long long kMaxBricks = kMaxSlots >> (3 * kLogB);
+constexpr size_t kScratchBytes = align256(kOffNbr + kMaxBricks * 27 * 4);
 static_assert(kScratchBytes <= (size_t)AMR_NOALLOC_SCRATCH_BYTES, "scratch larger than advertised");
 
 // The scratch itself. In host code this name is only a stand-in for the
@@ -137,6 +139,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
   float* scal = reinterpret_cast<float*>(base + kOffScal);
   unsigned* view = reinterpret_cast<unsigned*>(base + kOffView);
   uint4* duals = reinterpret_cast<uint4*>(base + kOffDuals);
+  int* nbr = reinterpret_cast<int*>(base + kOffNbr);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -181,7 +184,9 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
                                       st)));
     const int grid_slots = (int)std::max(1ll, std::min((n_slots + block - 1) / block, (long long)sms * 8));
     NA_TRY(rc_of(launch_resolve_views(kLogB, L, view, n_slots, 0, sc, grid_slots, block, st)));
-    NA_TRY(rc_of(launch_dual_cells(kLogB, L, n_bricks, duals, kMaxDuals, sc, st)));
+    const int grid_nb = (int)std::max(1ll, std::min((n_bricks * 27 + block - 1) / block, (long long)sms * 8));
+    NA_TRY(rc_of(launch_brick_neighbors(kLogB, L, n_bricks, nbr, grid_nb, st)));
+    NA_TRY(rc_of(launch_dual_cells(kLogB, L, nbr, n_bricks, duals, kMaxDuals, sc, st)));
     NA_TRY(read_counters(sc, &h, st));
     NA_TRY(err_bits(h.err));
     nd = (long long)h.n_dual;

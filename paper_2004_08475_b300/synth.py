@@ -277,8 +277,8 @@ def vortex_vorticity(x: torch.Tensor, params) -> torch.Tensor:
     return torch.sqrt((acc * acc).sum(1))
 
 
-BLOCK_TAU = 0.0035      # block split threshold (frozen; ~100M cells at full size)
-BLOCK_ISO = 0.02        # iso-value (frozen)
+BLOCK_TAU = 0.12        # split threshold on the variation of s (frozen: ~126M cells)
+BLOCK_ISO = 0.2         # iso-value near the triangle-count maximum (~9M triangles)
 
 
 def block_vortex(seed: int = 3, dims=(64, 32, 32), tau: float = BLOCK_TAU, iso: float = BLOCK_ISO,
@@ -286,14 +286,16 @@ def block_vortex(seed: int = 3, dims=(64, 32, 32), tau: float = BLOCK_TAU, iso: 
                  scale: float = 1.0):
     """Block-structured AMR without hierarchy. Level-3 blocks (8^3 cells of
     width 8, edge 64) tile a dims*64 domain; a level-l block splits into 8
-    level-(l-1) blocks iff s at one of its 8 octant centres exceeds tau; 5% of
-    the final blocks are removed as holes; every block expands to its 512
-    cells. `scale` shrinks ring geometry for small test domains."""
+    level-(l-1) blocks iff s varies by more than tau over its 8 octant centres
+    (refinement on variation, as block-AMR codes refine where the solution
+    changes); 5% of the final blocks are removed as holes; every block
+    expands to its 512 cells. `scale` shrinks ring geometry for small test
+    domains."""
     dom = [d * 64 for d in dims]
     prm = list(_ring_params(seed, n_rings, dom))
-    prm[2] = prm[2] * scale
-    prm[3] = prm[3] * scale
-    prm[4] = math.pi * prm[3] ** 2 * (prm[4] / (math.pi * (prm[3] / scale) ** 2))
+    prm[2] = prm[2] * scale          # ring radius
+    prm[3] = prm[3] * scale          # core radius
+    prm[4] = prm[4] * scale ** 2     # circulation, keeps the peak vorticity
     blocks = _grid(*dims, 64, device)
     l = 3
     out_b, out_l = [], []
@@ -307,7 +309,8 @@ def block_vortex(seed: int = 3, dims=(64, 32, 32), tau: float = BLOCK_TAU, iso: 
         vals = torch.empty(octs.shape[0], dtype=torch.float64, device=device)
         for a in range(0, octs.shape[0], chunk):
             vals[a:a + chunk] = vortex_vorticity(octs[a:a + chunk], prm)
-        split = vals.reshape(-1, 8).amax(1) > tau
+        v8 = vals.reshape(-1, 8)
+        split = (v8.amax(1) - v8.amin(1)) > tau
         out_b.append(blocks[~split])
         out_l.append(torch.full((int((~split).sum()),), l, dtype=torch.int64, device=device))
         blocks = _children(blocks[split], edge // 2)
@@ -352,11 +355,12 @@ def wing_sdf(x: torch.Tensor, wing) -> torch.Tensor:
     return torch.where((dx > 0) | (dy > 0) | (dz > 0), outside, inside)
 
 
-def lognormal_field(x: torch.Tensor, seed: int, n_waves: int = 64) -> torch.Tensor:
+def lognormal_field(x: torch.Tensor, seed: int, n_waves: int = 64, waves=(32.0, 512.0)) -> torch.Tensor:
     """s = exp(2 g), g = sqrt(2/n) sum_m cos(k_m . x + phi_m): a unit-variance
-    random-phase field, so s is log-normal with sigma = 2 (wavelengths 32-512)."""
+    random-phase field, so s is log-normal with sigma = 2 (wavelengths
+    log-uniform in `waves`)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    lam = np.exp(rng.uniform(math.log(32.0), math.log(512.0), size=n_waves))
+    lam = np.exp(rng.uniform(math.log(waves[0]), math.log(waves[1]), size=n_waves))
     dirs = rng.normal(size=(n_waves, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
     k = dirs * (2 * math.pi / lam)[:, None]
@@ -367,13 +371,17 @@ def lognormal_field(x: torch.Tensor, seed: int, n_waves: int = 64) -> torch.Tens
     return torch.exp(2.0 * g)
 
 
+# Frozen by probing cell and triangle counts: ~590M cells, ~130M triangles.
 WING_DIMS = (448, 448, 96)        # level-3 (width 8) root grid
-WING_BANDS = (22.0, 56.0, 120.0)  # |sdf| thresholds for widths 1, 2, 4
-WING_ISO = 40.0
+WING_BANDS = (75.0, 125.0, 195.0)  # |sdf| thresholds for widths 1, 2, 4
+WING_ISO = 2.7
+
+
+WING_WAVES = (12.0, 192.0)
 
 
 def wing_bands(seed: int = 4, dims=WING_DIMS, bands=WING_BANDS, iso: float = WING_ISO,
-               device="cpu", chunk: int = 1 << 24, scale: float = 1.0):
+               device="cpu", chunk: int = 1 << 24, scale: float = 1.0, waves=None):
     """Exajet-sized AMR: widths 1,2,4,8. The domain is tiled with width-8
     cells; a cell of width w splits while |sdf(centre)| < band(w/2); cells
     whose centre lies inside the wing (sdf < 0) are dropped as holes. The
@@ -406,7 +414,8 @@ def wing_bands(seed: int = 4, dims=WING_DIMS, bands=WING_BANDS, iso: float = WIN
     del out_x, out_l
     s = torch.empty(xyz.shape[0], dtype=torch.float32, device=device)
     for a in range(0, xyz.shape[0], chunk):
-        s[a:a + chunk] = lognormal_field(centres(xyz[a:a + chunk], level[a:a + chunk]), seed).float()
+        s[a:a + chunk] = lognormal_field(centres(xyz[a:a + chunk], level[a:a + chunk]), seed,
+                                         waves=waves or WING_WAVES).float()
     return _pack(xyz, level, s, iso, seed,
                  {"workload": "wing_bands", "domain": dom, "levels": 4, "bands": list(bands)})
 
