@@ -207,7 +207,7 @@ const char* amr_kernel_name(int k);
  * calls that overlap on the GPU (other host threads or streams) race.
  * Synchronises the stream. */
 #define AMR_NOALLOC_MAX_CELLS 65536
-#define AMR_NOALLOC_SCRATCH_BYTES (14u << 20)
+#define AMR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level,
                         const float* scalar, int64_t n, float iso, float* tris,
                         int64_t cap, int64_t* n_tris, void* cuda_stream);

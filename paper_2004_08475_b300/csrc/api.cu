@@ -72,7 +72,7 @@ struct amr_ctx {
   float alpha = 0.5f;
   int block = 256;
   int check_overlap = 0;
-  DevBuf hkeys, hvals, bricks, cell_id, scal, view, nbr;
+  DevBuf hkeys, hvals, bricks, rec, scal, view, nbr;
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
   int levels = 0;
@@ -198,7 +198,7 @@ Locator make_locator(amr_ctx* c) {
   L.hvals = static_cast<const int*>(c->hvals.p);
   L.hmask = c->hcap - 1;
   L.bricks = static_cast<const int4*>(c->bricks.p);
-  L.cell_id = static_cast<const int*>(c->cell_id.p);
+  L.rec = static_cast<const unsigned long long*>(c->rec.p);
   L.scal = static_cast<const float*>(c->scal.p);
   L.view = static_cast<const unsigned*>(c->view.p);
   L.levels = c->levels;
@@ -286,7 +286,7 @@ void amr_destroy(amr_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                    &c->cell_id, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch, &c->stage_buf,
+                    &c->rec, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch, &c->stage_buf,
                     &c->iso_buf, &c->seg_buf};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
@@ -364,11 +364,15 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   c->n_dual = -1;
   const long long n = c->n;
   const int B3 = 1 << (3 * logb);
-  // Expected bricks: every brick at least 1/8 full; retry with a bigger
-  // table when the real count says otherwise.
-  unsigned long long want = (unsigned long long)((double)(n * 8 / B3 + 64) / alpha);
+  // Table size: bricks expected at least 1/4 full, but start no larger than
+  // 2^22 entries (48 MB) so the table stays in L2 while every cell probes
+  // it. A table that fills up stops the insert early and is rebuilt larger.
+  unsigned long long want = (unsigned long long)((double)(n * 4 / B3 + 64) / alpha);
+  want = std::min<unsigned long long>(want, 1ull << 22);
   for (int attempt = 0;; ++attempt) {
     c->hcap = pow2_at_least(want);
+    const unsigned long long limit =
+        (unsigned long long)((double)c->hcap * std::min(0.85, 2.0 * (double)alpha));
     AMR_TRY(ensure(c->hkeys, c->hcap * 8));
     AMR_TRY(ensure(c->hvals, c->hcap * 4));
     AMR_TRY(ensure(c->bricks, c->hcap * 16));
@@ -379,7 +383,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
       AMR_CUDA(launch_insert_bricks(logb, c->xyz, c->lvl, c->s, n,
                                     static_cast<unsigned long long*>(c->hkeys.p),
                                     static_cast<int*>(c->hvals.p), c->hcap - 1,
-                                    static_cast<int4*>(c->bricks.p), dev_sc(c),
+                                    static_cast<int4*>(c->bricks.p), limit, dev_sc(c),
                                     grid_for(c, n, block, 2048 / block), block, c->stream));
     }
     AMR_TRY(read_scratch(c));
@@ -387,9 +391,9 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
     const unsigned full = h.err & ERR_HASH_FULL;
     const int rc = err_code(h.err & ~ERR_HASH_FULL);
     if (rc != AMR_OK) return rc;
-    if (full || (double)h.n_bricks > (double)c->hcap * std::min(0.85, 2.0 * alpha)) {
+    if (full) {
       if (attempt >= 4) return AMR_ERR_RANGE;
-      want = (unsigned long long)(std::max<double>((double)h.n_bricks, (double)want) * 4.0 / alpha);
+      want = (unsigned long long)(std::max<double>((double)h.n_bricks, (double)c->hcap) * 4.0 / alpha);
       continue;
     }
     c->n_bricks = (long long)h.n_bricks;
@@ -402,23 +406,23 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   }
   c->n_slots = c->n_bricks * B3;
   if (c->n_slots >= (long long)INT_MAX) return AMR_ERR_RANGE;
-  AMR_TRY(ensure(c->cell_id, (size_t)c->n_slots * 4));
+  AMR_TRY(ensure(c->rec, (size_t)c->n_slots * 8));
   AMR_TRY(ensure(c->scal, (size_t)c->n_slots * 4));
   AMR_TRY(ensure(c->view, (size_t)c->n_slots * 4));
   if (c->n_slots) {
-    AMR_CUDA(cudaMemsetAsync(c->cell_id.p, 0xFF, (size_t)c->n_slots * 4, c->stream));
+    AMR_CUDA(cudaMemsetAsync(c->rec.p, 0xFF, (size_t)c->n_slots * 8, c->stream));
     const Locator L = make_locator(c);
     {
       KernelTimer kt(c, KT_SCATTER);
-      AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, L, static_cast<int*>(c->cell_id.p),
-                                    static_cast<float*>(c->scal.p), dev_sc(c),
+      AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, L,
+                                    static_cast<unsigned long long*>(c->rec.p), dev_sc(c),
                                     grid_for(c, n, block, 2048 / block), block, c->stream));
     }
     {
       KernelTimer kt(c, KT_RESOLVE);
-      AMR_CUDA(launch_resolve_views(logb, L, static_cast<unsigned*>(c->view.p), c->n_slots, overlap,
-                                    dev_sc(c), grid_for(c, c->n_slots, block, 2048 / block), block,
-                                    c->stream));
+      AMR_CUDA(launch_resolve_views(logb, L, static_cast<unsigned*>(c->view.p), static_cast<float*>(c->scal.p),
+                                    c->n_slots, overlap, dev_sc(c), grid_for(c, c->n_slots, block, 2048 / block),
+                                    block, c->stream));
     }
     AMR_TRY(ensure(c->nbr, (size_t)c->n_bricks * 27 * 4));
     {
@@ -478,7 +482,8 @@ int amr_get_duals(amr_ctx* c, int32_t* out, int64_t cap, int flags) {
   {
     KernelTimer kt(c, KT_GET_DUALS);
     AMR_CUDA(launch_get_duals(static_cast<const uint4*>(c->duals.p), c->n_dual,
-                              static_cast<const int*>(c->cell_id.p), dst, grid_for(c, 2 * c->n_dual, 256, 8),
+                              static_cast<const unsigned long long*>(c->rec.p), dst,
+                              grid_for(c, 2 * c->n_dual, 256, 8),
                               c->stream));
   }
   AMR_TRY(deliver(c, out, dst, bytes, flags));
@@ -596,7 +601,7 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->n_levels = c->stage >= 2 ? c->levels : 0;
   info->log2_brick = c->logb;
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                          &c->cell_id, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch,
+                          &c->rec, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch,
                           &c->stage_buf, &c->iso_buf, &c->seg_buf};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);

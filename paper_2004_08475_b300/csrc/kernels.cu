@@ -7,9 +7,10 @@
 //                units) and its level; a level-l brick covers B^3 logical
 //                level-l cells, B = 2^LOGB
 //   slots        one per logical cell of every brick, Morton order inside a
-//                brick: cell_id[] (input index or -1), scal[] (its scalar),
-//                view[] (the slot of the actual cell containing the logical
-//                cell: itself, a coarser cell, or kReject)
+//                brick: rec[] (8 bytes: input index and scalar bits of the
+//                occupant, all ones when empty), scal[] (its scalar), view[]
+//                (the slot of the actual cell containing the logical cell:
+//                itself, a coarser cell, or kReject)
 //   dual cells   duals[D] = 2 x uint4: the 8 vertex slots, order ex+2ey+4ez
 //   triangles    tris[T][3][3] f32
 //
@@ -107,7 +108,7 @@ template <int LOGB>
 __global__ void __launch_bounds__(1024) k_insert_bricks(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
     const float* __restrict__ s, long long n, unsigned long long* hkeys, int* hvals,
-    unsigned long long hmask, int4* bricks, Scratch* sc) {
+    unsigned long long hmask, int4* bricks, unsigned long long brick_limit, Scratch* sc) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -116,6 +117,8 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   int ml = 0;
   unsigned err = 0;
   for (long long base = wid * 32; base < n; base += nwarps * 32) {
+    // the host rebuilds a table that filled up: stop early
+    if (__any_sync(kFull, (__ldcg(&sc->err) & ERR_HASH_FULL) != 0u)) break;
     const long long i = base + lane;
     unsigned long long key = kEmptyKey;
     int x = 0, y = 0, z = 0, l = 0;
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
           const unsigned long long prev = atomicCAS(hkeys + h, kEmptyKey, key);
           if (prev == kEmptyKey) {
             const unsigned long long bi = atomicAdd(&sc->n_bricks, 1ull);
+            if (bi >= brick_limit) atomicOr(&sc->err, (unsigned)ERR_HASH_FULL);
             hvals[h] = (int)bi;
             const int m = ~((1 << (l + LOGB)) - 1);
             bricks[bi] = make_int4(x & m, y & m, z & m, l);
@@ -212,12 +216,13 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   }
 }
 
-// Pass 2 over the cells: put every cell into its brick slot. Two cells in one
-// slot are a duplicate label (i,j,k;l).
+// Pass 2 over the cells: put every cell (index and scalar) into its brick
+// slot. Two cells in one slot are a duplicate label (i,j,k;l). Finite
+// scalars never produce the all-ones empty pattern.
 template <int LOGB>
 __global__ void __launch_bounds__(1024) k_scatter_cells(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
-    const float* __restrict__ s, long long n, Locator L, int* cell_id, float* scal, Scratch* sc) {
+    const float* __restrict__ s, long long n, Locator L, unsigned long long* rec, Scratch* sc) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -245,8 +250,9 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
         err |= ERR_HASH_FULL;
       } else {
         const long long slot = ((long long)bi << (3 * LOGB)) | local_index<LOGB>(x, y, z, l);
-        if (atomicCAS(cell_id + slot, -1, (int)i) != -1) err |= ERR_DUPLICATE;
-        scal[slot] = v;
+        // one 8-byte record per cell: a single random sector per cell
+        const unsigned long long r = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned)i;
+        if (atomicCAS(rec + slot, kEmptyRec, r) != kEmptyRec) err |= ERR_DUPLICATE;
       }
     }
   }
@@ -260,28 +266,30 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
 // check_overlap, an occupied slot that is also covered by a coarser cell
 // flags ERR_OVERLAP.
 template <int LOGB>
-__global__ void __launch_bounds__(1024) k_resolve_views(Locator L, unsigned* view, long long n_slots,
-                                                       int check_overlap, Scratch* sc) {
+__global__ void __launch_bounds__(1024) k_resolve_views(Locator L, unsigned* view, float* scal,
+                                                       long long n_slots, int check_overlap, Scratch* sc) {
   unsigned err = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x; slot < n_slots;
        slot += stride) {
     const int4 c = slot_cell<LOGB>(L.bricks, (unsigned)slot);
-    const int id = L.cell_id[slot];
-    unsigned v = id >= 0 ? (unsigned)slot : kReject;
-    if (id < 0 || check_overlap) {
+    const unsigned long long r = L.rec[slot];
+    const bool occupied = r != kEmptyRec;
+    unsigned v = occupied ? (unsigned)slot : kReject;
+    if (!occupied || check_overlap) {
       for (int lv = c.w + 1; lv < L.levels; ++lv) {
         const int bj = find_brick(L, brick_key<LOGB>(c.x, c.y, c.z, lv));
         if (bj < 0) continue;
         const unsigned s2 = ((unsigned)bj << (3 * LOGB)) | local_index<LOGB>(c.x, c.y, c.z, lv);
-        if (__ldg(L.cell_id + s2) >= 0) {
-          if (id >= 0) err |= ERR_OVERLAP;
+        if (__ldg(L.rec + s2) != kEmptyRec) {
+          if (occupied) err |= ERR_OVERLAP;
           else v = s2;
           break;
         }
       }
     }
     view[slot] = v;
+    scal[slot] = occupied ? __uint_as_float((unsigned)(r >> 32)) : 0.f;
   }
   if (err) atomicOr(&sc->err, err);
 }
@@ -354,11 +362,13 @@ __constant__ DualMasks c_masks = make_dual_masks();
 // One CTA per brick, one thread per brick slot. The CTA loads the brick's
 // resolved views plus a one-cell halo ((B+2)^3 entries, from the 26
 // neighbouring bricks of the same level or the first coarser brick that
-// covers them) into shared memory; each thread then decides the 8 duals of
-// its cell: a dual is emitted iff every vertex exists (rule 1), none is finer
-// (rule 2, finer regions resolve to kReject) and every same-level vertex
-// comes after the cell in (z,y,x) order (rule 3). Survivors are compacted
-// with one atomic per CTA.
+// covers them) into shared memory, marking same-level cells in bit 31, and
+// condenses every row of the region into a mask (bit x: a cell exists, bit
+// 16+x: it is of this brick's level). Each thread then reads 9 row masks and
+// decides the 8 duals of its cell: a dual is emitted iff every vertex exists
+// (rule 1), none is finer (rule 2: finer regions resolve to kReject) and
+// every same-level vertex comes after the cell in (z,y,x) order (rule 3).
+// Survivors are compacted with one atomic per CTA.
 template <int LOGB>
 __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
     Locator L, const int* __restrict__ nbr, long long n_bricks, uint4* __restrict__ duals, long long cap,
@@ -368,8 +378,9 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
   constexpr int NT = B * B * B;
   constexpr int NR = R * R * R;
   constexpr int NW = (NT + 31) / 32;
+  constexpr unsigned kSame = 0x80000000u;   // slot indices stay below 2^31
   __shared__ unsigned rv[NR];
-  __shared__ unsigned char rs[NR];
+  __shared__ unsigned rmask[R * R];
   __shared__ int nb[27];
   __shared__ unsigned wsum[NW];
   __shared__ unsigned long long cta_base;
@@ -382,11 +393,12 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
     const int4 b = __ldg(L.bricks + bi);
     const int l = b.w;
     if (t < 27) nb[t] = __ldg(nbr + bi * 27 + t);
+    bool mine;
     {   // the brick itself: one coalesced read, slot t is this thread's cell
       const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)t;
       const unsigned v = __ldg(L.view + s2);
-      rv[cself] = v;
-      rs[cself] = v == s2;
+      mine = v == s2;
+      rv[cself] = mine ? (v | kSame) : v;
     }
     __syncthreads();
     for (int r = t; r < NR; r += NT) {   // the one-cell halo
@@ -396,27 +408,38 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
                       9 * (rz == 0 ? 0 : (rz == R - 1 ? 2 : 1));
       const int e = nb[nbi];
       unsigned v = kReject;
-      unsigned char same = 0;
       if (e >= 0) {
         const int fb = e & ((1 << 27) - 1), lv = e >> 27;
         const int x = b.x + ((rx - 1) << l), y = b.y + ((ry - 1) << l), z = b.z + ((rz - 1) << l);
         const unsigned s2 = ((unsigned)fb << (3 * LOGB)) | local_index<LOGB>(x, y, z, lv);
         v = __ldg(L.view + s2);
-        same = (lv == l) && (v == s2);
+        if (lv == l && v == s2) v |= kSame;
       }
       rv[r] = v;
-      rs[r] = same;
+    }
+    __syncthreads();
+    for (int row = t; row < R * R; row += NT) {
+      unsigned m = 0;
+#pragma unroll
+      for (int rx = 0; rx < R; ++rx) {
+        const unsigned v = rv[row * R + rx];
+        if (v != kReject) m |= (1u << rx) | ((v >> 31) << (16 + rx));
+      }
+      rmask[row] = m;
     }
     __syncthreads();
     unsigned emit = 0;
-    if (rs[cself]) {   // this slot holds an actual level-l cell
+    if (mine) {   // this slot holds an actual level-l cell
       unsigned exist = 0, samem = 0;
 #pragma unroll
-      for (int o = 0; o < 27; ++o) {
-        const int r = c0 + (o % 3) + R * ((o / 3) % 3) + R * R * (o / 9);
-        exist |= (rv[r] != kReject ? 1u : 0u) << o;
-        samem |= (unsigned)rs[r] << o;
-      }
+      for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+          const unsigned m = rmask[(py + oy) + R * (pz + oz)];
+          const int sh = 3 * oy + 9 * oz;
+          exist |= ((m >> px) & 7u) << sh;
+          samem |= ((m >> (16 + px)) & 7u) << sh;
+        }
 #pragma unroll
       for (int d = 0; d < 8; ++d) {
         const bool ok = ((exist & c_masks.all[d]) == c_masks.all[d]) && !(samem & c_masks.lower[d]);
@@ -451,7 +474,7 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
       unsigned v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e)
-        v[e] = rv[c0 + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2))];
+        v[e] = rv[c0 + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2))] & ~kSame;
       if (idx < cap) {
         duals[2 * idx] = make_uint4(v[0], v[1], v[2], v[3]);
         duals[2 * idx + 1] = make_uint4(v[4], v[5], v[6], v[7]);
@@ -614,7 +637,7 @@ __device__ __forceinline__ int case_of(const unsigned v[8], float sv[8], const f
 // atomic per warp and write their interpolated vertices. Optionally writes
 // per-dual case and triangle count instead.
 template <int LOGB, bool EMIT, bool CASES>
-__global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
+__global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
                                             float iso, float* __restrict__ tris, long long cap,
                                             unsigned long long* counter, unsigned char* cases,
                                             unsigned char* ntri, const __grid_constant__ McConst mc) {
@@ -780,12 +803,13 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
 }
 
 __global__ void __launch_bounds__(256) k_get_duals(const uint4* __restrict__ duals, long long nd,
-                                                   const int* __restrict__ cell_id, int* __restrict__ out) {
+                                                   const unsigned long long* __restrict__ rec,
+                                                   int* __restrict__ out) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nd; i += stride) {
     const uint4 a = __ldg(duals + i);
-    reinterpret_cast<int4*>(out)[i] =
-        make_int4(__ldg(cell_id + a.x), __ldg(cell_id + a.y), __ldg(cell_id + a.z), __ldg(cell_id + a.w));
+    reinterpret_cast<int4*>(out)[i] = make_int4((int)__ldg(rec + a.x), (int)__ldg(rec + a.y),
+                                                (int)__ldg(rec + a.z), (int)__ldg(rec + a.w));
   }
 }
 
@@ -808,24 +832,26 @@ __global__ void __launch_bounds__(256) k_get_duals(const uint4* __restrict__ dua
 
 cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
                                  long long n, unsigned long long* hkeys, int* hvals,
-                                 unsigned long long hmask, int4* bricks, Scratch* sc, int grid,
-                                 int block, cudaStream_t st) {
+                                 unsigned long long hmask, int4* bricks,
+                                 unsigned long long brick_limit, Scratch* sc, int grid, int block,
+                                 cudaStream_t st) {
   AMR_DISPATCH(logb, (k_insert_bricks<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, hkeys, hvals, hmask,
-                                                                   bricks, sc)));
+                                                                   bricks, brick_limit, sc)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* lvl, const float* s,
-                                 long long n, Locator loc, int* cell_id, float* scal, Scratch* sc,
+                                 long long n, Locator loc, unsigned long long* rec, Scratch* sc,
                                  int grid, int block, cudaStream_t st) {
-  AMR_DISPATCH(logb, (k_scatter_cells<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, loc, cell_id, scal, sc)));
+  AMR_DISPATCH(logb, (k_scatter_cells<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, loc, rec, sc)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, long long n_slots,
+cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, float* scal, long long n_slots,
                                  int check_overlap, Scratch* sc, int grid, int block,
                                  cudaStream_t st) {
-  AMR_DISPATCH(logb, (k_resolve_views<LB><<<grid, block, 0, st>>>(loc, view, n_slots, check_overlap, sc)));
+  AMR_DISPATCH(logb, (k_resolve_views<LB><<<grid, block, 0, st>>>(loc, view, scal, n_slots, check_overlap,
+                                                                   sc)));
   return cudaGetLastError();
 }
 
@@ -876,10 +902,10 @@ cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long
   return cudaGetLastError();
 }
 
-cudaError_t launch_get_duals(const uint4* duals, long long nd, const int* cell_id, int* out, int grid,
-                             cudaStream_t st) {
+cudaError_t launch_get_duals(const uint4* duals, long long nd, const unsigned long long* rec, int* out,
+                             int grid, cudaStream_t st) {
   if (nd <= 0) return cudaSuccess;
-  k_get_duals<<<grid, 256, 0, st>>>(duals, nd, cell_id, out);
+  k_get_duals<<<grid, 256, 0, st>>>(duals, nd, rec, out);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@ namespace amriso {
 
 constexpr uint32_t kReject = 0xFFFFFFFFu;          // "does not exist" in a view
 constexpr unsigned long long kEmptyKey = ~0ull;     // free hash slot
+constexpr unsigned long long kEmptyRec = ~0ull;     // free brick slot
 constexpr int kMaxLevel = 14;                       // levels 0..14
 constexpr int kMaxIso = 64;                         // iso-values per batch
 
@@ -40,7 +41,8 @@ struct Locator {
   const int* hvals;                 // [hcap] brick index
   unsigned long long hmask;         // hcap - 1 (hcap a power of two)
   const int4* bricks;               // [n_bricks] origin x,y,z (finest units), level
-  const int* cell_id;               // [n_slots] input index of the slot's cell or -1
+  const unsigned long long* rec;    // [n_slots] occupant: input index (low 32 bits, all ones
+                                    //   when empty) and scalar bits (high 32 bits)
   const float* scal;                // [n_slots] scalar of the slot's cell
   const unsigned* view;             // [n_slots] resolved cell slot, or kReject
   int levels;                       // max level + 1
@@ -57,16 +59,21 @@ struct McConst {
 // ---- launches (all asynchronous on `st`) --------------------------------
 // Each returns the launch's cudaError_t (cudaGetLastError after launch).
 
+// brick_limit: once this many bricks exist the table counts as full
+// (ERR_HASH_FULL is raised and the remaining inserts stop early).
 cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
                                  long long n, unsigned long long* hkeys, int* hvals,
-                                 unsigned long long hmask, int4* bricks, Scratch* sc,
-                                 int grid, int block, cudaStream_t st);
+                                 unsigned long long hmask, int4* bricks,
+                                 unsigned long long brick_limit, Scratch* sc, int grid, int block,
+                                 cudaStream_t st);
 
+// rec must be all ones (kEmptyRec) before the launch.
 cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* lvl, const float* s,
-                                 long long n, Locator loc, int* cell_id, float* scal, Scratch* sc,
+                                 long long n, Locator loc, unsigned long long* rec, Scratch* sc,
                                  int grid, int block, cudaStream_t st);
 
-cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, long long n_slots,
+// Writes view[] and scal[] of every slot from rec[].
+cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, float* scal, long long n_slots,
                                  int check_overlap, Scratch* sc, int grid, int block,
                                  cudaStream_t st);
 
@@ -91,7 +98,7 @@ cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long
                                  const long long* seg_off, Scratch* sc, const McConst& mc,
                                  int grid, long long tile, cudaStream_t st);
 
-cudaError_t launch_get_duals(const uint4* duals, long long nd, const int* cell_id, int* out,
+cudaError_t launch_get_duals(const uint4* duals, long long nd, const unsigned long long* rec, int* out,
                              int grid, cudaStream_t st);
 
 }  // namespace amriso

@@ -38,8 +38,8 @@ constexpr size_t kOffScratch = 0;
 constexpr size_t kOffKeys = align256(kOffScratch + sizeof(Scratch));
 constexpr size_t kOffVals = align256(kOffKeys + kHashCap * 8);
 constexpr size_t kOffBricks = align256(kOffVals + kHashCap * 4);
-constexpr size_t kOffCellId = align256(kOffBricks + kMaxCells * 16);   // a brick holds >= 1 cell
-constexpr size_t kOffScal = align256(kOffCellId + kMaxSlots * 4);
+constexpr size_t kOffRec = align256(kOffBricks + kMaxCells * 16);   // a brick holds >= 1 cell
+constexpr size_t kOffScal = align256(kOffRec + kMaxSlots * 8);
 constexpr size_t kOffView = align256(kOffScal + kMaxSlots * 4);
 constexpr size_t kOffDuals = align256(kOffView + kMaxSlots * 4);
 constexpr size_t kOffNbr = align256(kOffDuals + kMaxDuals * 32);
@@ -135,7 +135,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
   unsigned long long* hkeys = reinterpret_cast<unsigned long long*>(base + kOffKeys);
   int* hvals = reinterpret_cast<int*>(base + kOffVals);
   int4* bricks = reinterpret_cast<int4*>(base + kOffBricks);
-  int* cell_id = reinterpret_cast<int*>(base + kOffCellId);
+  unsigned long long* rec = reinterpret_cast<unsigned long long*>(base + kOffRec);
   float* scal = reinterpret_cast<float*>(base + kOffScal);
   unsigned* view = reinterpret_cast<unsigned*>(base + kOffView);
   uint4* duals = reinterpret_cast<uint4*>(base + kOffDuals);
@@ -156,8 +156,8 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
   const int block = 256;
   const int grid_cells = (int)std::max(1ll, std::min((long long)(n + block - 1) / block, (long long)sms * 8));
   if (n > 0)
-    NA_TRY(rc_of(launch_insert_bricks(kLogB, xyz, level, scalar, n, hkeys, hvals, kHashCap - 1, bricks, sc,
-                                      grid_cells, block, st)));
+    NA_TRY(rc_of(launch_insert_bricks(kLogB, xyz, level, scalar, n, hkeys, hvals, kHashCap - 1, bricks,
+                                      kMaxCells, sc, grid_cells, block, st)));
   NA_TRY(read_counters(sc, &h, st));
   NA_TRY(err_bits(h.err));
   const long long n_bricks = (long long)h.n_bricks;
@@ -173,17 +173,16 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
   L.hvals = hvals;
   L.hmask = kHashCap - 1;
   L.bricks = bricks;
-  L.cell_id = cell_id;
+  L.rec = rec;
   L.scal = scal;
   L.view = view;
   L.levels = n > 0 ? h.max_level + 1 : 0;
   long long nd = 0;
   if (n_slots > 0) {
-    NA_TRY(rc_of(cudaMemsetAsync(cell_id, 0xFF, (size_t)n_slots * 4, st)));
-    NA_TRY(rc_of(launch_scatter_cells(kLogB, xyz, level, scalar, n, L, cell_id, scal, sc, grid_cells, block,
-                                      st)));
+    NA_TRY(rc_of(cudaMemsetAsync(rec, 0xFF, (size_t)n_slots * 8, st)));
+    NA_TRY(rc_of(launch_scatter_cells(kLogB, xyz, level, scalar, n, L, rec, sc, grid_cells, block, st)));
     const int grid_slots = (int)std::max(1ll, std::min((n_slots + block - 1) / block, (long long)sms * 8));
-    NA_TRY(rc_of(launch_resolve_views(kLogB, L, view, n_slots, 0, sc, grid_slots, block, st)));
+    NA_TRY(rc_of(launch_resolve_views(kLogB, L, view, scal, n_slots, 0, sc, grid_slots, block, st)));
     const int grid_nb = (int)std::max(1ll, std::min((n_bricks * 27 + block - 1) / block, (long long)sms * 8));
     NA_TRY(rc_of(launch_brick_neighbors(kLogB, L, n_bricks, nbr, grid_nb, st)));
     NA_TRY(rc_of(launch_dual_cells(kLogB, L, nbr, n_bricks, duals, kMaxDuals, sc, st)));
