@@ -433,6 +433,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
     AMR_TRY(read_scratch(c));
     const int rc = err_code(c->host_sc->err);
     if (rc != AMR_OK) return rc;
+    if ((long long)c->host_sc->n_occupied != n) return AMR_ERR_DUPLICATE;  // two cells, one slot
   }
   c->stage = 2;
   return AMR_OK;

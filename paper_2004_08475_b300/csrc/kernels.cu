@@ -101,9 +101,13 @@ __device__ __forceinline__ unsigned warp_or(unsigned v) { return __reduce_or_syn
 // Locator build (Sec. 3.2)
 // ---------------------------------------------------------------------------
 
+constexpr int kUnroll = 4;   // cells per lane per trip of the cell-parallel loops
+
 // Pass 1 over the cells: validate, take the bounding box and the deepest
 // level, and insert every cell's brick key into the hash table. The CAS
-// winner of a key numbers the brick and records its corner and level.
+// winner of a key numbers the brick and records its corner and level. Each
+// lane takes kUnroll cells per trip, loads hoisted, so that their memory
+// latencies overlap; one lane per distinct key in a warp touches the table.
 template <int LOGB>
 __global__ void __launch_bounds__(1024) k_insert_bricks(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
@@ -116,57 +120,76 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   int hi0 = INT_MIN, hi1 = INT_MIN, hi2 = INT_MIN;
   int ml = 0;
   unsigned err = 0;
-  for (long long base = wid * 32; base < n; base += nwarps * 32) {
-    // the host rebuilds a table that filled up: stop early
+  // a table this crowded is rebuilt larger by the host: fail fast
+  const unsigned long long limit = hmask < 4095ull ? hmask + 1 : 4096ull;
+  for (long long base = wid * 32 * kUnroll; base < n; base += nwarps * 32 * kUnroll) {
     if (__any_sync(kFull, (__ldcg(&sc->err) & ERR_HASH_FULL) != 0u)) break;
-    const long long i = base + lane;
-    unsigned long long key = kEmptyKey;
-    int x = 0, y = 0, z = 0, l = 0;
-    if (i < n) {
-      x = xyz[3 * i];
-      y = xyz[3 * i + 1];
-      z = xyz[3 * i + 2];
-      l = lvl[i];
-      if (!isfinite(s[i])) err |= ERR_NONFINITE;
-      if (l > kMaxLevel) {
-        err |= ERR_RANGE;
-      } else if ((x | y | z) & ((1 << l) - 1)) {
-        err |= ERR_UNALIGNED;
-      } else {
-        const long long w = 1ll << l;
-        lo0 = min(lo0, x);
-        lo1 = min(lo1, y);
-        lo2 = min(lo2, z);
-        hi0 = max(hi0, (int)min((long long)x + w, (long long)INT_MAX));
-        hi1 = max(hi1, (int)min((long long)y + w, (long long)INT_MAX));
-        hi2 = max(hi2, (int)min((long long)z + w, (long long)INT_MAX));
-        ml = max(ml, l);
-        key = brick_key<LOGB>(x, y, z, l);
+    int x[kUnroll], y[kUnroll], z[kUnroll], l[kUnroll];
+    float v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const long long i = base + u * 32 + lane;
+      x[u] = y[u] = z[u] = 0;
+      l[u] = -1;
+      v[u] = 0.f;
+      if (i < n) {
+        x[u] = __ldg(xyz + 3 * i);
+        y[u] = __ldg(xyz + 3 * i + 1);
+        z[u] = __ldg(xyz + 3 * i + 2);
+        l[u] = __ldg(lvl + i);
+        v[u] = __ldg(s + i);
       }
     }
-    const unsigned peers = __match_any_sync(kFull, key);
-    if (key != kEmptyKey && lane == __ffs(peers) - 1) {
-      unsigned long long h = mix64(key) & hmask;
+    unsigned long long key[kUnroll], h[kUnroll], cur[kUnroll];
+    bool lead[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      key[u] = kEmptyKey;
+      if (l[u] >= 0) {
+        if (!isfinite(v[u])) err |= ERR_NONFINITE;
+        if (l[u] > kMaxLevel) {
+          err |= ERR_RANGE;
+        } else if ((x[u] | y[u] | z[u]) & ((1 << l[u]) - 1)) {
+          err |= ERR_UNALIGNED;
+        } else {
+          const long long w = 1ll << l[u];
+          lo0 = min(lo0, x[u]);
+          lo1 = min(lo1, y[u]);
+          lo2 = min(lo2, z[u]);
+          hi0 = max(hi0, (int)min((long long)x[u] + w, (long long)INT_MAX));
+          hi1 = max(hi1, (int)min((long long)y[u] + w, (long long)INT_MAX));
+          hi2 = max(hi2, (int)min((long long)z[u] + w, (long long)INT_MAX));
+          ml = max(ml, l[u]);
+          key[u] = brick_key<LOGB>(x[u], y[u], z[u], l[u]);
+        }
+      }
+      const unsigned peers = __match_any_sync(kFull, key[u]);
+      lead[u] = key[u] != kEmptyKey && lane == __ffs(peers) - 1;
+      h[u] = mix64(key[u]) & hmask;
+      cur[u] = lead[u] ? __ldcg(hkeys + h[u]) : 0ull;   // independent first probes
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (!lead[u] || cur[u] == key[u]) continue;
+      unsigned long long hh = h[u];
       bool done = false;
-      // a table this crowded is rebuilt larger by the host: fail fast
-      const unsigned long long limit = hmask < 4095ull ? hmask + 1 : 4096ull;
       for (unsigned long long p = 0; p < limit; ++p) {
-        const unsigned long long cur = __ldcg(hkeys + h);
-        if (cur == key) { done = true; break; }
-        if (cur == kEmptyKey) {
-          const unsigned long long prev = atomicCAS(hkeys + h, kEmptyKey, key);
+        const unsigned long long c = p == 0 ? cur[u] : __ldcg(hkeys + hh);
+        if (c == key[u]) { done = true; break; }
+        if (c == kEmptyKey) {
+          const unsigned long long prev = atomicCAS(hkeys + hh, kEmptyKey, key[u]);
           if (prev == kEmptyKey) {
             const unsigned long long bi = atomicAdd(&sc->n_bricks, 1ull);
             if (bi >= brick_limit) atomicOr(&sc->err, (unsigned)ERR_HASH_FULL);
-            hvals[h] = (int)bi;
-            const int m = ~((1 << (l + LOGB)) - 1);
-            bricks[bi] = make_int4(x & m, y & m, z & m, l);
+            hvals[hh] = (int)bi;
+            const int m = ~((1 << (l[u] + LOGB)) - 1);
+            bricks[bi] = make_int4(x[u] & m, y[u] & m, z[u] & m, l[u]);
             done = true;
             break;
           }
-          if (prev == key) { done = true; break; }
+          if (prev == key[u]) { done = true; break; }
         }
-        h = (h + 1) & hmask;
+        hh = (hh + 1) & hmask;
       }
       if (!done) err |= ERR_HASH_FULL;
     }
@@ -216,9 +239,11 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   }
 }
 
-// Pass 2 over the cells: put every cell (index and scalar) into its brick
-// slot. Two cells in one slot are a duplicate label (i,j,k;l). Finite
-// scalars never produce the all-ones empty pattern.
+// Pass 2 over the cells: store every cell (index and scalar bits, one
+// 8-byte record) into its brick slot with a plain store - no atomic, so the
+// random writes do not wait on each other. A duplicate label (i,j,k;l) makes
+// two cells share a slot; the slot pass below then counts fewer occupied
+// slots than cells. Finite scalars never form the all-ones empty pattern.
 template <int LOGB>
 __global__ void __launch_bounds__(1024) k_scatter_cells(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
@@ -227,33 +252,43 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   unsigned err = 0;
-  for (long long base = wid * 32; base < n; base += nwarps * 32) {
-    const long long i = base + lane;
-    unsigned long long key = kEmptyKey;
-    int x = 0, y = 0, z = 0, l = 0;
-    float v = 0.f;
-    if (i < n) {
-      x = xyz[3 * i];
-      y = xyz[3 * i + 1];
-      z = xyz[3 * i + 2];
-      l = lvl[i];
-      v = s[i];
-      if (l <= kMaxLevel) key = brick_key<LOGB>(x, y, z, l);
+  for (long long base = wid * 32 * kUnroll; base < n; base += nwarps * 32 * kUnroll) {
+    int x[kUnroll], y[kUnroll], z[kUnroll], l[kUnroll];
+    float v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const long long i = base + u * 32 + lane;
+      x[u] = y[u] = z[u] = 0;
+      l[u] = -1;
+      v[u] = 0.f;
+      if (i < n) {
+        x[u] = __ldg(xyz + 3 * i);
+        y[u] = __ldg(xyz + 3 * i + 1);
+        z[u] = __ldg(xyz + 3 * i + 2);
+        l[u] = __ldg(lvl + i);
+        v[u] = __ldg(s + i);
+      }
     }
-    const unsigned peers = __match_any_sync(kFull, key);
-    const int leader = __ffs(peers) - 1;
-    int bi = -1;
-    if (key != kEmptyKey && lane == leader) bi = find_brick(L, key);
-    bi = __shfl_sync(kFull, bi, leader);
-    if (key != kEmptyKey) {
+    unsigned long long key[kUnroll], k0[kUnroll];
+    int b0[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {   // first probe of every key, issued together
+      key[u] = (l[u] >= 0 && l[u] <= kMaxLevel) ? brick_key<LOGB>(x[u], y[u], z[u], l[u]) : kEmptyKey;
+      const unsigned long long h = mix64(key[u]) & L.hmask;
+      k0[u] = key[u] != kEmptyKey ? __ldg(L.hkeys + h) : kEmptyKey;
+      b0[u] = key[u] != kEmptyKey ? __ldg(L.hvals + h) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (key[u] == kEmptyKey) continue;
+      const int bi = k0[u] == key[u] ? b0[u] : find_brick(L, key[u]);
       if (bi < 0) {
         err |= ERR_HASH_FULL;
-      } else {
-        const long long slot = ((long long)bi << (3 * LOGB)) | local_index<LOGB>(x, y, z, l);
-        // one 8-byte record per cell: a single random sector per cell
-        const unsigned long long r = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned)i;
-        if (atomicCAS(rec + slot, kEmptyRec, r) != kEmptyRec) err |= ERR_DUPLICATE;
+        continue;
       }
+      const long long i = base + u * 32 + lane;
+      const long long slot = ((long long)bi << (3 * LOGB)) | local_index<LOGB>(x[u], y[u], z[u], l[u]);
+      rec[slot] = ((unsigned long long)__float_as_uint(v[u]) << 32) | (unsigned)i;
     }
   }
   err = warp_or(err);
@@ -269,6 +304,7 @@ template <int LOGB>
 __global__ void __launch_bounds__(1024) k_resolve_views(Locator L, unsigned* view, float* scal,
                                                        long long n_slots, int check_overlap, Scratch* sc) {
   unsigned err = 0;
+  unsigned occ = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x; slot < n_slots;
        slot += stride) {
@@ -290,8 +326,19 @@ __global__ void __launch_bounds__(1024) k_resolve_views(Locator L, unsigned* vie
     }
     view[slot] = v;
     scal[slot] = occupied ? __uint_as_float((unsigned)(r >> 32)) : 0.f;
+    occ += occupied ? 1u : 0u;
   }
   if (err) atomicOr(&sc->err, err);
+  // occupied-slot count (duplicate labels show as fewer slots than cells)
+  __shared__ unsigned occ_w[32];
+  occ = __reduce_add_sync(kFull, occ);
+  if ((threadIdx.x & 31) == 0) occ_w[threadIdx.x >> 5] = occ;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned t = threadIdx.x < (blockDim.x >> 5) ? occ_w[threadIdx.x] : 0u;
+    t = __reduce_add_sync(kFull, t);
+    if (threadIdx.x == 0 && t) atomicAdd(&sc->n_occupied, (unsigned long long)t);
+  }
 }
 
 // Pass over (brick, neighbour) pairs: for every brick its 26 neighbouring
@@ -359,23 +406,32 @@ __host__ __device__ constexpr DualMasks make_dual_masks() {
 
 __constant__ DualMasks c_masks = make_dual_masks();
 
-// One CTA per brick, one thread per brick slot. The CTA loads the brick's
-// resolved views plus a one-cell halo ((B+2)^3 entries, from the 26
-// neighbouring bricks of the same level or the first coarser brick that
-// covers them) into shared memory, marking same-level cells in bit 31, and
-// condenses every row of the region into a mask (bit x: a cell exists, bit
-// 16+x: it is of this brick's level). Each thread then reads 9 row masks and
-// decides the 8 duals of its cell: a dual is emitted iff every vertex exists
-// (rule 1), none is finer (rule 2: finer regions resolve to kReject) and
-// every same-level vertex comes after the cell in (z,y,x) order (rule 3).
-// Survivors are compacted with one atomic per CTA.
+// Threads of the dual-cell CTA: one per brick slot up to 256, so that eight
+// CTAs fit an SM at B = 8 (each thread then owns two cells).
 template <int LOGB>
-__global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
+struct DualShape {
+  static constexpr int kCells = 1 << (3 * LOGB);
+  static constexpr int kThreads = kCells < 256 ? kCells : 256;
+  static constexpr int kPerThread = kCells / kThreads;
+};
+
+// One CTA per brick. The CTA loads the brick's resolved views plus a
+// one-cell halo ((B+2)^3 entries, from the 26 neighbouring bricks of the same
+// level or the first coarser brick that covers them) into shared memory,
+// marking same-level cells in bit 31, and condenses every row of the region
+// into a mask (bit x: a cell exists, bit 16+x: it is of this brick's level).
+// Each cell then reads 9 row masks and decides its 8 duals: a dual is emitted
+// iff every vertex exists (rule 1), none is finer (rule 2: finer regions
+// resolve to kReject) and every same-level vertex comes after the cell in
+// (z,y,x) order (rule 3). Survivors are compacted with one atomic per CTA.
+template <int LOGB>
+__global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     Locator L, const int* __restrict__ nbr, long long n_bricks, uint4* __restrict__ duals, long long cap,
     Scratch* sc) {
   constexpr int B = 1 << LOGB;
   constexpr int R = B + 2;
-  constexpr int NT = B * B * B;
+  constexpr int NT = DualShape<LOGB>::kThreads;
+  constexpr int CPT = DualShape<LOGB>::kPerThread;
   constexpr int NR = R * R * R;
   constexpr int NW = (NT + 31) / 32;
   constexpr unsigned kSame = 0x80000000u;   // slot indices stay below 2^31
@@ -386,19 +442,26 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
   __shared__ unsigned long long cta_base;
   const int t = threadIdx.x;
   const int lane = t & 31, wp = t >> 5;
-  const int px = compact<LOGB>(t), py = compact<LOGB>(t >> 1), pz = compact<LOGB>(t >> 2);
-  const int c0 = px + R * (py + R * pz);   // neighbourhood origin (cell - 1) in the region
-  const int cself = c0 + 1 + R + R * R;    // this thread's own cell in the region
+  int c0[CPT], px[CPT], py[CPT], pz[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int m = t + j * NT;   // Morton index of the cell inside the brick
+    px[j] = compact<LOGB>(m);
+    py[j] = compact<LOGB>(m >> 1);
+    pz[j] = compact<LOGB>(m >> 2);
+    c0[j] = px[j] + R * (py[j] + R * pz[j]);   // neighbourhood origin (cell - 1)
+  }
   for (long long bi = blockIdx.x; bi < n_bricks; bi += gridDim.x) {
     const int4 b = __ldg(L.bricks + bi);
     const int l = b.w;
     if (t < 27) nb[t] = __ldg(nbr + bi * 27 + t);
-    bool mine;
-    {   // the brick itself: one coalesced read, slot t is this thread's cell
-      const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)t;
+    bool mine[CPT];
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {   // the brick itself: coalesced reads
+      const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)(t + j * NT);
       const unsigned v = __ldg(L.view + s2);
-      mine = v == s2;
-      rv[cself] = mine ? (v | kSame) : v;
+      mine[j] = v == s2;
+      rv[c0[j] + 1 + R + R * R] = mine[j] ? (v | kSame) : v;
     }
     __syncthreads();
     for (int r = t; r < NR; r += NT) {   // the one-cell halo
@@ -428,26 +491,30 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
       rmask[row] = m;
     }
     __syncthreads();
-    unsigned emit = 0;
-    if (mine) {   // this slot holds an actual level-l cell
+    unsigned emit[CPT];
+    unsigned cnt = 0;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      emit[j] = 0;
+      if (!mine[j]) continue;   // the slot holds no level-l cell
       unsigned exist = 0, samem = 0;
 #pragma unroll
       for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
         for (int oy = 0; oy < 3; ++oy) {
-          const unsigned m = rmask[(py + oy) + R * (pz + oz)];
+          const unsigned m = rmask[(py[j] + oy) + R * (pz[j] + oz)];
           const int sh = 3 * oy + 9 * oz;
-          exist |= ((m >> px) & 7u) << sh;
-          samem |= ((m >> (16 + px)) & 7u) << sh;
+          exist |= ((m >> px[j]) & 7u) << sh;
+          samem |= ((m >> (16 + px[j])) & 7u) << sh;
         }
 #pragma unroll
       for (int d = 0; d < 8; ++d) {
         const bool ok = ((exist & c_masks.all[d]) == c_masks.all[d]) && !(samem & c_masks.lower[d]);
-        emit |= (ok ? 1u : 0u) << d;
+        emit[j] |= (ok ? 1u : 0u) << d;
       }
+      cnt += __popc(emit[j]);
     }
     // CTA-wide exclusive scan of the per-thread dual counts
-    const unsigned cnt = __popc(emit);
     unsigned incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -468,18 +535,21 @@ __global__ void __launch_bounds__(1 << (3 * LOGB)) k_dual_cells(
     __syncthreads();
     long long idx = (long long)cta_base + wsum[wp] + incl - cnt;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) {
-      if (!((emit >> d) & 1u)) continue;
-      const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
-      unsigned v[8];
+    for (int j = 0; j < CPT; ++j) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        v[e] = rv[c0 + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2))] & ~kSame;
-      if (idx < cap) {
-        duals[2 * idx] = make_uint4(v[0], v[1], v[2], v[3]);
-        duals[2 * idx + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+      for (int d = 0; d < 8; ++d) {
+        if (!((emit[j] >> d) & 1u)) continue;
+        const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+        unsigned v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          v[e] = rv[c0[j] + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2))] & ~kSame;
+        if (idx < cap) {
+          duals[2 * idx] = make_uint4(v[0], v[1], v[2], v[3]);
+          duals[2 * idx + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+        }
+        ++idx;
       }
-      ++idx;
     }
     __syncthreads();
   }
@@ -866,7 +936,8 @@ cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, long long n
                               long long cap, Scratch* sc, cudaStream_t st) {
   if (n_bricks <= 0) return cudaSuccess;
   const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
-  AMR_DISPATCH(logb, (k_dual_cells<LB><<<grid, 1 << (3 * LB), 0, st>>>(loc, nbr, n_bricks, duals, cap, sc)));
+  AMR_DISPATCH(logb, (k_dual_cells<LB><<<grid, DualShape<LB>::kThreads, 0, st>>>(loc, nbr, n_bricks, duals,
+                                                                                 cap, sc)));
   return cudaGetLastError();
 }
 

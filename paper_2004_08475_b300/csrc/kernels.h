@@ -29,6 +29,7 @@ struct Scratch {
   unsigned long long n_dual;
   unsigned long long tile;              // persistent-kernel work counter
   unsigned long long n_tri[kMaxIso];    // per iso-value triangle counters
+  unsigned long long n_occupied;        // occupied brick slots (= cells unless duplicates)
   unsigned int err;
   int lo[3];                            // bounding box: min lower corner
   int hi[3];                            // max (lower corner + width)

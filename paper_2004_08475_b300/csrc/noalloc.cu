@@ -188,6 +188,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
     NA_TRY(rc_of(launch_dual_cells(kLogB, L, nbr, n_bricks, duals, kMaxDuals, sc, st)));
     NA_TRY(read_counters(sc, &h, st));
     NA_TRY(err_bits(h.err));
+    if ((long long)h.n_occupied != n) return AMR_ERR_DUPLICATE;   // two cells shared a slot
     nd = (long long)h.n_dual;
     if (nd > kMaxDuals) return AMR_ERR_RANGE;
   }
