@@ -139,6 +139,17 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def reduce_over_ranks(ms: float, nd: int, nt: int, dist, device) -> tuple:
+    """Max step time over ranks and summed dual / triangle counts (the
+    replicas share no data; only the timing and totals are combined)."""
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([float(nd), float(nt)], dtype=torch.float64, device=device)
+    dist.all_reduce(tot)
+    nd_all, nt_all = tot.tolist()
+    return float(t.item()), nd_all, nt_all
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle leg (bounded sample)
 # ---------------------------------------------------------------------------
@@ -221,6 +232,92 @@ def run_reference(args, workload_desc, gen):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving workload: 24 data sets of 50k..50M cells, Zipf(1) popularity,
+    Poisson arrivals of requests with 1-16 iso-values; the continuous-batching
+    server against per-request plain extraction (FIFO), at 0.5/0.8/0.95 of the
+    plain path's measured capacity, plus one run under an 8 GB budget."""
+    from paper_2004_08475_b300 import serve
+    torch.cuda.set_device(0)
+    sets = synth.serving_set(device="cuda")
+    host = {name: (x.cpu().pin_memory(), l.cpu().pin_memory(), v.cpu().pin_memory())
+            for name, x, l, v, _ in sets}
+    iso_rng = {name: r for name, _, _, _, r in sets}
+    names = [t[0] for t in sets]
+    del sets
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(5)
+    pop = 1.0 / np.arange(1, len(names) + 1)
+    perm = rng.permutation(len(names))                       # popularity unrelated to size
+    prob = np.empty(len(names))
+    prob[perm] = pop / pop.sum()
+
+    def make(nreq, arrivals):
+        reqs = []
+        for i in range(nreq):
+            name = names[rng.choice(len(names), p=prob)]
+            a, b = iso_rng[name]
+            isos = list(rng.uniform(a, b, size=int(rng.integers(1, 17))))
+            reqs.append(serve.Request(i, name, [float(v) for v in isos], float(arrivals[i])))
+        return reqs
+
+    # plain capacity: back-to-back service of a sample
+    sample = make(args.serve_sample, np.zeros(args.serve_sample))
+    t0 = time.perf_counter()
+    for r in sample:
+        r.t_arrival = t0
+    serve.serve_plain(host, sample)
+    cap_plain = len(sample) / (max(r.t_done for r in sample) - t0)
+
+    def run_server(reqs, budget):
+        srv = serve.Server(budget_bytes=budget, slots=args.serve_slots)
+        for name, (x, l, v) in host.items():
+            srv.datasets[name] = serve._Dataset(name, x, l, v, {})
+        srv.start()
+        t_base = time.perf_counter() + 0.05
+        for r in reqs:
+            r.t_arrival += t_base
+        for r in reqs:
+            now = time.perf_counter()
+            if r.t_arrival > now:
+                time.sleep(r.t_arrival - now)
+            with srv.cv:
+                srv.queue.append(r)
+                srv.cv.notify_all()
+        for r in reqs:
+            r.done.wait()
+        stats = dict(srv.stats)
+        srv.stop()
+        return {**serve.latency_summary(reqs), "stats": stats}
+
+    def run_plain(reqs):
+        t_base = time.perf_counter() + 0.05
+        for r in reqs:
+            r.t_arrival += t_base
+        serve.serve_plain(host, reqs)
+        return serve.latency_summary(reqs)
+
+    results = {}
+    for load in (0.5, 0.8, 0.95):
+        rate = load * cap_plain
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_requests))
+        reqs = make(args.serve_requests, arr)
+        clone = [serve.Request(r.rid, r.dataset, list(r.isos), r.t_arrival) for r in reqs]
+        results[str(load)] = {"rate_per_s": rate, "server": run_server(reqs, 120 << 30),
+                              "plain": run_plain(clone)}
+    arr = np.cumsum(rng.exponential(1.0 / (0.8 * cap_plain), size=args.serve_requests))
+    results["0.8_budget_8GB"] = {"server": run_server(make(args.serve_requests, arr), 8 << 30)}
+    line = {"mode": "serve", "metric": METRIC, "unit": "ms (p50/p99 latency), triangles/s",
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "serving: 24 data sets 50k-50M cells (octree / block crops), Zipf(1), "
+                                   "Poisson arrivals, 1-16 iso-values per request",
+                       "requests_per_load": args.serve_requests, "slots": args.serve_slots,
+                       "budget_gb": 120},
+            "plain_capacity_req_per_s": cap_plain, "loads": results,
+            "gpu": torch.cuda.get_device_name(0)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,7 +331,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--batch-isos", type=int, default=16)
+    ap.add_argument("--mode", default="step", choices=["step", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-sample", type=int, default=80)
+    ap.add_argument("--serve-slots", type=int, default=3)
     args = ap.parse_args()
+    if args.mode == "serve":
+        run_serve(args)
+        return
     args.warmup = max(args.warmup, 3)
     desc, gen = WORKLOADS[args.workload]
 
@@ -295,12 +399,7 @@ def main():
     ctx.enable_timing(False)
     inf = ctx.info()
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([float(nd), float(nt)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tot)
-        nd_all, nt_all = tot.tolist()
+        ms, nd_all, nt_all = reduce_over_ranks(ms, nd, nt, dist, "cuda")
     else:
         nd_all, nt_all = float(nd), float(nt)
 

@@ -147,6 +147,20 @@ int amr_iso_cases(amr_ctx* ctx, float iso, uint8_t* cases, uint8_t* ntri,
 int amr_iso_batch(amr_ctx* ctx, const float* isos, int n_iso, float* tris,
                   int64_t cap, int64_t* offsets, int flags);
 
+/* amr_iso_batch without any host synchronisation or allocation, for use
+ * inside a captured CUDA graph: the iso-values are read from device memory
+ * when the work runs, and the segment offsets are computed on the device.
+ *   d_isos    [n_iso] device array, 1 <= n_iso <= 64
+ *   tris      [cap][3][3] device output; iso k's triangles are rows
+ *             d_offsets[k] .. d_offsets[k+1]-1 (rows past cap are dropped)
+ *   d_offsets [n_iso+1] device int64 written by the device; the caller reads
+ *             it after the stream completes and compares d_offsets[n_iso]
+ *             with cap.
+ * Requires amr_dual_cells to have completed on this context. Returns after
+ * enqueuing. */
+int amr_iso_batch_async(amr_ctx* ctx, const float* d_isos, int n_iso,
+                        float* tris, int64_t cap, int64_t* d_offsets);
+
 /* Waits for all work queued on the context's stream. */
 int amr_sync(amr_ctx* ctx);
 

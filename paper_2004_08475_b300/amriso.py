@@ -78,6 +78,7 @@ def _load() -> ctypes.CDLL:
         "amr_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), I]),
         "amr_iso_cases": (I, [P, F, P, P, I]),
         "amr_iso_batch": (I, [P, P, I, P, I64, P, I]),
+        "amr_iso_batch_async": (I, [P, P, I, P, I64, P]),
         "amr_sync": (I, [P]),
         "amr_strerror": (ctypes.c_char_p, [I]),
         "amr_mc_table": (I, [P, P]),
@@ -100,7 +101,7 @@ _lib = _load()
 EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_build_locator",
            "amr_dual_cells", "amr_get_duals", "amr_iso", "amr_iso_cases", "amr_iso_batch",
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
-           "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc")
+           "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async")
 
 
 def lib() -> ctypes.CDLL:
@@ -267,6 +268,14 @@ class AmrContext:
                                     offs.ctypes.data, flags)
         _check(rc, "amr_iso_batch")
         return out[:int(offs[-1])], torch.from_numpy(offs)
+
+    def iso_batch_async(self, d_isos: torch.Tensor, out: torch.Tensor, d_offsets: torch.Tensor):
+        """Enqueue a batched extraction (iso-values and offsets on the device);
+        no host synchronisation, so it can be captured in a CUDA graph."""
+        assert d_isos.is_cuda and d_isos.dtype == torch.float32 and d_offsets.dtype == torch.int64
+        assert d_offsets.numel() >= d_isos.numel() + 1 and out.is_cuda
+        _check(_lib.amr_iso_batch_async(self._h, _ptr(d_isos), int(d_isos.numel()), _ptr(out),
+                                        int(out.shape[0]), _ptr(d_offsets)), "amr_iso_batch_async")
 
     def sync(self):
         _check(_lib.amr_sync(self._h), "amr_sync")

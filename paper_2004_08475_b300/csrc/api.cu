@@ -444,6 +444,8 @@ int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
   if (c->stage < 2) return AMR_ERR_STATE;
   AMR_CUDA(cudaSetDevice(c->device));
   long long cap = std::max(c->dual_cap, c->n + c->n / 4 + 1024);
+  AMR_TRY(ensure(c->iso_buf, sizeof(float) * kMaxIso));
+  AMR_TRY(ensure(c->seg_buf, sizeof(long long) * (kMaxIso + 1)));
   for (int attempt = 0; attempt < 2; ++attempt) {
     AMR_TRY(ensure(c->duals, (size_t)cap * 32));
     c->dual_cap = (long long)(c->duals.bytes / 32);
@@ -585,11 +587,35 @@ int amr_iso_batch(amr_ctx* c, const float* isos, int n_iso, float* tris, int64_t
   AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->tile, 0, sizeof(unsigned long long), c->stream));
   {
     KernelTimer kt(c, KT_BATCH_EMIT);
-    AMR_CUDA(launch_mc_batch_emit(c->logb, L, du, nd, d_iso, n_iso, dst, d_off, dev_sc(c), c->mc,
+    AMR_CUDA(launch_mc_batch_emit(c->logb, L, du, nd, d_iso, n_iso, dst, d_off, run, dev_sc(c), c->mc,
                                   grid, 4096, c->stream));
   }
   if (flags & AMR_HOST_PTRS) AMR_TRY(deliver(c, tris, dst, (size_t)run * 36, flags));
   AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return AMR_OK;
+}
+
+int amr_iso_batch_async(amr_ctx* c, const float* d_isos, int n_iso, float* tris, int64_t cap,
+                        int64_t* d_offsets) {
+  if (!c || !d_isos || !d_offsets || n_iso < 1 || n_iso > kMaxIso || cap < 0 || (cap > 0 && !tris))
+    return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  const long long nd = c->n_dual;
+  const Locator L = make_locator(c);
+  const uint4* du = static_cast<const uint4*>(c->duals.p);
+  AMR_CUDA(cudaMemsetAsync(dev_sc(c)->n_tri, 0, sizeof(unsigned long long) * kMaxIso, c->stream));
+  {
+    KernelTimer kt(c, KT_BATCH_COUNT);
+    AMR_CUDA(launch_mc_batch_count(c->logb, L, du, nd, d_isos, n_iso, dev_sc(c), c->mc,
+                                   grid_for(c, nd, 256, 8), c->stream));
+  }
+  AMR_CUDA(launch_batch_offsets(dev_sc(c), n_iso, reinterpret_cast<long long*>(d_offsets), c->stream));
+  {
+    KernelTimer kt(c, KT_BATCH_EMIT);
+    AMR_CUDA(launch_mc_batch_emit(c->logb, L, du, nd, d_isos, n_iso, tris,
+                                  reinterpret_cast<const long long*>(d_offsets), cap, dev_sc(c), c->mc,
+                                  c->sm_count * 8, 4096, c->stream));
+  }
   return AMR_OK;
 }
 

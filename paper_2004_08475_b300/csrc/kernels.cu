@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   unsigned err = 0;
   // a table this crowded is rebuilt larger by the host: fail fast
   const unsigned long long limit = hmask < 4095ull ? hmask + 1 : 4096ull;
+  int trip = 0;
   for (long long base = wid * 32 * kUnroll; base < n; base += nwarps * 32 * kUnroll) {
-    if (__any_sync(kFull, (__ldcg(&sc->err) & ERR_HASH_FULL) != 0u)) break;
+    if ((trip++ & 31) == 0 && __any_sync(kFull, (__ldcg(&sc->err) & ERR_HASH_FULL) != 0u)) break;
     int x[kUnroll], y[kUnroll], z[kUnroll], l[kUnroll];
     float v[kUnroll];
 #pragma unroll
@@ -707,7 +708,7 @@ __device__ __forceinline__ int case_of(const unsigned v[8], float sv[8], const f
 // atomic per warp and write their interpolated vertices. Optionally writes
 // per-dual case and triangle count instead.
 template <int LOGB, bool EMIT, bool CASES>
-__global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
+__global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
                                             float iso, float* __restrict__ tris, long long cap,
                                             unsigned long long* counter, unsigned char* cases,
                                             unsigned char* ntri, const __grid_constant__ McConst mc) {
@@ -811,8 +812,9 @@ template <int LOGB>
 __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* __restrict__ duals,
                                                        long long nd, const float* __restrict__ isos,
                                                        int n_iso, float* __restrict__ tris,
-                                                       const long long* __restrict__ seg_off, Scratch* sc,
-                                                       long long tile, const __grid_constant__ McConst mc) {
+                                                       const long long* __restrict__ seg_off, long long total_cap,
+                                                       Scratch* sc, long long tile,
+                                                       const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
   __shared__ float iso_sh[kMaxIso];
   __shared__ long long off_sh[kMaxIso + 1];
@@ -862,7 +864,9 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
         if (__ballot_sync(kFull, keep != 0) == 0) continue;
         const long long idx = warp_append(__popc(keep), &sc->n_tri[k]);
         if (keep) {
-          const long long cap = off_sh[k + 1] - off_sh[k];
+          // rows of segment k that fit the buffer (all of them unless the
+          // caller's capacity was short)
+          const long long cap = max(0ll, min(off_sh[k + 1], total_cap) - off_sh[k]);
           stage_row(vr, sr, v, sv);
           write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[cas], keep, idx, cap, tris + 9 * off_sh[k],
                                 mc.edge_a, mc.edge_b);
@@ -870,6 +874,21 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
       }
     }
   }
+}
+
+// Device-side segment offsets of a batch: exclusive prefix of the per-iso
+// counts of the count pass; resets the counters and the tile counter for the
+// emit pass. One thread; n_iso <= kMaxIso.
+__global__ void k_batch_offsets(Scratch* sc, int n_iso, long long* off) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long run = 0;
+  for (int k = 0; k < n_iso; ++k) {
+    off[k] = run;
+    run += (long long)sc->n_tri[k];
+    sc->n_tri[k] = 0;
+  }
+  off[n_iso] = run;
+  sc->tile = 0;
 }
 
 __global__ void __launch_bounds__(256) k_get_duals(const uint4* __restrict__ duals, long long nd,
@@ -965,11 +984,16 @@ cudaError_t launch_mc_batch_count(int logb, Locator loc, const uint4* duals, lon
 
 cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long long nd,
                                  const float* isos, int n_iso, float* tris, const long long* seg_off,
-                                 Scratch* sc, const McConst& mc, int grid, long long tile,
-                                 cudaStream_t st) {
+                                 long long total_cap, Scratch* sc, const McConst& mc, int grid,
+                                 long long tile, cudaStream_t st) {
   if (nd <= 0) return cudaSuccess;
   AMR_DISPATCH(logb, (k_mc_batch_emit<LB><<<grid, 256, 0, st>>>(loc, duals, nd, isos, n_iso, tris, seg_off,
-                                                                 sc, tile, mc)));
+                                                                 total_cap, sc, tile, mc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_offsets(Scratch* sc, int n_iso, long long* off, cudaStream_t st) {
+  k_batch_offsets<<<1, 32, 0, st>>>(sc, n_iso, off);
   return cudaGetLastError();
 }
 

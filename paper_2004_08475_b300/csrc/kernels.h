@@ -94,10 +94,14 @@ cudaError_t launch_mc_batch_count(int logb, Locator loc, const uint4* duals, lon
                                   const float* isos, int n_iso, Scratch* sc, const McConst& mc,
                                   int grid, cudaStream_t st);
 
+// Segment k gets rows seg_off[k] .. seg_off[k+1]-1, clipped to total_cap.
 cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long long nd,
                                  const float* isos, int n_iso, float* tris,
-                                 const long long* seg_off, Scratch* sc, const McConst& mc,
-                                 int grid, long long tile, cudaStream_t st);
+                                 const long long* seg_off, long long total_cap, Scratch* sc,
+                                 const McConst& mc, int grid, long long tile, cudaStream_t st);
+
+// off[0..n_iso] = exclusive prefix of sc->n_tri; resets n_tri and tile.
+cudaError_t launch_batch_offsets(Scratch* sc, int n_iso, long long* off, cudaStream_t st);
 
 cudaError_t launch_get_duals(const uint4* duals, long long nd, const unsigned long long* rec, int* out,
                              int grid, cudaStream_t st);

@@ -428,17 +428,40 @@ def serving_sizes(count: int = 24, lo: float = 5e4, hi: float = 5e7):
     return [int(lo * (hi / lo) ** (i / (count - 1))) for i in range(count)]
 
 
-def serving_dataset(i: int, target: int, device="cpu"):
-    """Data set i of the serving mix: octree style for even i, block style for
-    odd i; level depth cycles 2..5; sized to about `target` cells."""
-    depth = 2 + (i % 4)
-    if i % 2 == 0:
-        # octree: roots of width 2^(depth-1); cells grow ~ with root count
-        r = max(2, int(round((target / 40.0) ** (1.0 / 3.0))))
-        out = octree_gaussians(seed=1000 + i, roots=r, root_level=depth - 1,
-                               tau=OCTREE_TAU * (r / 32.0), device=device)
-    else:
-        nb = max(1, int(round((target / 512.0 / 2.2) ** (1.0 / 3.0))))
-        out = block_vortex(seed=1000 + i, dims=(nb, nb, nb), device=device,
-                           scale=nb / 32.0, tau=BLOCK_TAU)
+def crop(xyz, level, s, target: int, seed: int):
+    """The cells inside a box around a finest-level cell, the box grown or
+    shrunk until it holds about `target` cells (a crop of an AMR data set is
+    an AMR data set whose border acts as a hole)."""
+    g = torch.Generator(device="cpu").manual_seed(int(seed))
+    fine = torch.nonzero(level == level.min()).reshape(-1)
+    c = xyz[fine[torch.randint(0, fine.shape[0], (1,), generator=g)]].to(torch.float64).reshape(1, 3)
+    x = xyz.to(torch.float64)
+    lo, hi = x.min(0).values, x.max(0).values
+    half = (hi - lo) * min(1.0, target / xyz.shape[0]) ** (1 / 3) / 2 + 1
+    m = None
+    for _ in range(60):
+        m = ((x - c).abs() <= half).all(1)
+        k = int(m.sum())
+        if 0.9 * target <= k <= 1.1 * target or k == xyz.shape[0]:
+            break
+        half = half * (target / max(k, 1)) ** (1 / 3)
+    return xyz[m].contiguous(), level[m].contiguous(), s[m].contiguous()
+
+
+def serving_set(count: int = 24, lo: float = 5e4, hi: float = 5e7, device="cpu"):
+    """Serving mix: `count` data sets of lo..hi cells (geometric sizes), cut
+    alternately from the octree workload (5 levels) and the block-structured
+    workload (4 levels, holes); sizes above the octree's ~10M cells come from
+    the block workload. Returns [(name, xyz, level, scalar, (iso_lo, iso_hi))]
+    with iso_lo/hi the 40th/95th percentiles of the data set's scalar."""
+    oct_ = octree_gaussians(device=device)
+    blk = block_vortex(device=device)
+    out = []
+    for i, n in enumerate(serving_sizes(count, lo, hi)):
+        src = oct_ if (i % 2 == 0 and n <= 0.8 * oct_[4]["n"]) else blk
+        x, l, v = crop(src[0], src[1], src[2], n, seed=500 + i)
+        srt = torch.sort(v).values
+        lo_q = float(srt[int(0.40 * (v.shape[0] - 1))])
+        hi_q = float(srt[int(0.95 * (v.shape[0] - 1))])
+        out.append((f"ds{i:02d}_{src[4]['workload']}", x, l, v, (lo_q, hi_q)))
     return out

@@ -1,0 +1,134 @@
+"""Serving: scheduling logic on the CPU (fake resident contexts), and on the
+GPU every request's result in a mixed, concurrently batched stream (with LRU
+eviction under a small budget and CUDA-graph replays) equals the same
+request served alone by the plain context path."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+
+class _FakeCtx:
+    def __init__(self):
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def _server(budget):
+    from paper_2004_08475_b300.serve import Server, _Resident
+    srv = Server.__new__(Server)
+    srv.budget = budget
+    srv.datasets = {}
+    srv.resident = __import__("collections").OrderedDict()
+    srv.queue = []
+    srv.cv = threading.Condition()
+    srv.used = 0
+    srv.stats = __import__("collections").Counter()
+    srv._rid = 0
+    return srv, _Resident
+
+
+def _req(rid, ds, k):
+    from paper_2004_08475_b300.serve import Request
+    return Request(rid, ds, [0.5] * k, time.perf_counter())
+
+
+def test_batch_coalesces_same_dataset_up_to_64_isos():
+    srv, _ = _server(1 << 30)
+    srv.queue = [_req(1, "a", 10), _req(2, "b", 3), _req(3, "a", 40), _req(4, "a", 20), _req(5, "a", 5)]
+    with srv.cv:
+        batch = srv._take_batch()
+    assert [r.rid for r in batch] == [1, 3, 5]          # 10 + 40 + 5 <= 64; 20 would exceed
+    assert [r.rid for r in srv.queue] == [2, 4]
+
+
+def test_batch_skips_dataset_in_use():
+    srv, Res = _server(1 << 30)
+    busy = Res("a", _FakeCtx(), 10)
+    busy.users = 1
+    srv.resident["a"] = busy
+    srv.queue = [_req(1, "a", 1), _req(2, "b", 1)]
+    with srv.cv:
+        batch = srv._take_batch()
+    assert [r.rid for r in batch] == [2]
+
+
+def test_lru_eviction_under_budget():
+    from paper_2004_08475_b300 import serve
+    srv, Res = _server(1000)
+
+    class D:
+        def __init__(self, n):
+            self.xyz = torch.zeros((n, 3))
+    srv.datasets = {"a": D(4), "b": D(4), "c": D(4)}
+    old = serve.BYTES_PER_CELL_ESTIMATE
+    serve.BYTES_PER_CELL_ESTIMATE = 100          # 400 bytes per data set
+    try:
+        for name in ("a", "b"):
+            with srv.cv:
+                res, fresh = srv._admit(name)
+            assert fresh
+            res.ctx = _FakeCtx()
+            res.users = 0
+        with srv.cv:                              # touch a: b becomes least recent
+            res, fresh = srv._admit("a")
+        assert not fresh
+        res.users = 0
+        victim_ctx = srv.resident["b"].ctx
+        with srv.cv:
+            res, fresh = srv._admit("c")          # 1200 > 1000: evict b
+        assert fresh and "b" not in srv.resident and victim_ctx.closed
+        assert srv.stats["evictions"] == 1 and srv.used == 800
+    finally:
+        serve.BYTES_PER_CELL_ESTIMATE = old
+
+
+@pytest.mark.gpu
+def test_mix_equals_alone():
+    from paper_2004_08475_b300 import amriso, synth
+    from paper_2004_08475_b300.serve import Server
+    from tests.parity import canonical
+    data = {
+        "sphere": synth.sphere_tiny()[:4],
+        "oct": synth.octree_gaussians(seed=31, roots=6, root_level=4)[:4],
+        "rnd": synth.random_octree(5, levels=4, roots=5, p_hole=0.05)[:4],
+        "blk": synth.block_vortex(seed=33, dims=(3, 2, 2), scale=0.1, tau=0.01, iso=0.05)[:4],
+    }
+    rng = np.random.default_rng(0)
+    srv = Server(budget_bytes=60 << 20, slots=3, keep_results=True, out_capacity=1 << 16)
+    for name, (x, l, s, iso) in data.items():
+        srv.add_dataset(name, x, l, s)
+    srv.start()
+    reqs = []
+    names = list(data)
+    for i in range(40):
+        name = names[rng.integers(len(names))]
+        s = data[name][2]
+        qs = rng.uniform(0.3, 0.8, size=int(rng.integers(1, 6)))
+        isos = [float(np.quantile(s.numpy(), q)) for q in qs]
+        reqs.append(srv.submit(name, isos))
+        if i % 7 == 0:
+            time.sleep(0.01)
+    for r in reqs:
+        assert r.done.wait(120)
+    srv.stop()
+    assert all(r.error is None for r in reqs), [r.error for r in reqs if r.error]
+    assert srv.stats["prefills"] > len(data)          # the budget forced evictions
+    assert srv.stats["graph_replays"] > 0
+    assert any(r.batched_with > 1 for r in reqs)
+    ctxs = {}
+    for name, (x, l, s, iso) in data.items():
+        c = amriso.AmrContext()
+        c.upload(x.cuda(), l.cuda(), s.cuda())
+        c.build_locator()
+        c.dual_cells()
+        ctxs[name] = c
+    for r in reqs:
+        for v, got in zip(r.isos, r.tris):
+            want = ctxs[r.dataset].iso(v).cpu().numpy()
+            assert got.shape[0] == want.shape[0]
+            assert (canonical(got.numpy()) == canonical(want)).all()
