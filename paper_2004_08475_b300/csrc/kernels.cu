@@ -106,8 +106,9 @@ constexpr int kUnroll = 4;   // cells per lane per trip of the cell-parallel loo
 // Pass 1 over the cells: validate, take the bounding box and the deepest
 // level, and insert every cell's brick key into the hash table. The CAS
 // winner of a key numbers the brick and records its corner and level. Each
-// lane takes kUnroll cells per trip, loads hoisted, so that their memory
-// latencies overlap; one lane per distinct key in a warp touches the table.
+// lane takes kUnroll cells per trip, loads and first probes hoisted, so that
+// their memory latencies overlap. Lanes holding the same key simply both
+// find it (or race on one CAS, which one of them wins).
 template <int LOGB>
 __global__ void __launch_bounds__(1024) k_insert_bricks(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
@@ -164,8 +165,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
           key[u] = brick_key<LOGB>(x[u], y[u], z[u], l[u]);
         }
       }
-      const unsigned peers = __match_any_sync(kFull, key[u]);
-      lead[u] = key[u] != kEmptyKey && lane == __ffs(peers) - 1;
+      lead[u] = key[u] != kEmptyKey;
       h[u] = mix64(key[u]) & hmask;
       cur[u] = lead[u] ? __ldcg(hkeys + h[u]) : 0ull;   // independent first probes
     }
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
   __shared__ unsigned rv[NR];
   __shared__ unsigned rmask[R * R];
   __shared__ int nb[27];
-  __shared__ unsigned wsum[NW];
+  __shared__ unsigned wsum[NW + 1];
   __shared__ unsigned long long cta_base;
   const int t = threadIdx.x;
   const int lane = t & 31, wp = t >> 5;
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     }
     __syncthreads();
     unsigned emit[CPT];
-    unsigned cnt = 0;
+    unsigned cnt = 0;   // per-thread dual count of cell j in bits 16j..16j+15
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {
       emit[j] = 0;
@@ -513,9 +513,11 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
         const bool ok = ((exist & c_masks.all[d]) == c_masks.all[d]) && !(samem & c_masks.lower[d]);
         emit[j] |= (ok ? 1u : 0u) << d;
       }
-      cnt += __popc(emit[j]);
+      cnt += (unsigned)__popc(emit[j]) << (16 * j);
     }
-    // CTA-wide exclusive scan of the per-thread dual counts
+    // CTA-wide exclusive scan of the packed counts: the duals of all cells
+    // t (first half) come before those of all cells t + NT, keeping the
+    // output in the brick's Morton order (totals stay below 2^16)
     unsigned incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -531,12 +533,19 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
         wsum[w] = run;
         run += x;
       }
-      cta_base = run ? atomicAdd(&sc->n_dual, (unsigned long long)run) : 0ull;
+      wsum[NW] = run;   // packed per-half totals
+      unsigned tot = 0;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) tot += (run >> (16 * j)) & 0xFFFFu;
+      cta_base = tot ? atomicAdd(&sc->n_dual, (unsigned long long)tot) : 0ull;
     }
     __syncthreads();
-    long long idx = (long long)cta_base + wsum[wp] + incl - cnt;
+    const unsigned excl = wsum[wp] + incl - cnt;
+    long long half_base = (long long)cta_base;
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {
+      long long idx = half_base + ((excl >> (16 * j)) & 0xFFFFu);
+      half_base += (wsum[NW] >> (16 * j)) & 0xFFFFu;
 #pragma unroll
       for (int d = 0; d < 8; ++d) {
         if (!((emit[j] >> d) & 1u)) continue;

@@ -20,6 +20,7 @@ from __future__ import annotations
 import collections
 import threading
 import time
+import traceback
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -89,6 +90,10 @@ class Server:
         self.workers = []
         self.stats = collections.Counter()
         self._rid = 0
+        # Graph capture must not overlap device allocation or release in other
+        # threads (context creation, locator buffers, eviction, buffer growth);
+        # kernel work and graph replays run outside this lock.
+        self.cuda_lock = threading.Lock()
 
     # -- registry ------------------------------------------------------------
     def add_dataset(self, name: str, xyz, lvl, s, **opts):
@@ -121,7 +126,8 @@ class Server:
             th.join()
         self.workers = []
         for r in list(self.resident.values()):
-            r.ctx.close()
+            if r.ctx is not None:
+                r.ctx.close()
         self.resident.clear()
         self.used = 0
 
@@ -146,20 +152,24 @@ class Server:
 
     def _admit(self, name: str):
         """Make room for `name` (LRU eviction of idle data sets) and mark it in
-        use. Caller holds cv; may wait until memory frees up."""
+        use. Caller holds cv; may wait until memory frees up. Returns the
+        resident entry, whether it still needs its dual-mesh pass, and the
+        evicted contexts (to be closed by the caller outside cv)."""
+        evicted = []
         while True:
             res = self.resident.get(name)
             if res is not None:
                 res.users += 1
                 self.resident.move_to_end(name)
-                return res, False
+                return res, False, evicted
             need = self.datasets[name].xyz.shape[0] * BYTES_PER_CELL_ESTIMATE
             while self.used + need > self.budget:
                 victim = next((r for r in self.resident.values() if r.users == 0), None)
                 if victim is None:
                     break
                 self.resident.pop(victim.name)
-                victim.ctx.close()
+                if victim.ctx is not None:
+                    evicted.append(victim.ctx)
                 self.used -= victim.bytes
                 self.stats["evictions"] += 1
             if self.used + need <= self.budget or not self.resident:
@@ -167,7 +177,7 @@ class Server:
                 res.users = 1
                 self.resident[name] = res
                 self.used += need
-                return res, True
+                return res, True, evicted
             self.cv.wait(0.01)
 
     def _release(self, res: _Resident):
@@ -178,10 +188,11 @@ class Server:
     # -- worker ----------------------------------------------------------------
     def _worker(self, w: int):
         torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(self.device)
-        out = torch.empty((self.out_capacity, 3, 3), dtype=torch.float32, device=self.device)
-        d_isos = torch.empty(MAX_ISOS, dtype=torch.float32, device=self.device)
-        d_offs = torch.zeros(MAX_ISOS + 1, dtype=torch.int64, device=self.device)
+        with self.cuda_lock:
+            stream = torch.cuda.Stream(self.device)
+            out = torch.empty((self.out_capacity, 3, 3), dtype=torch.float32, device=self.device)
+            d_isos = torch.empty(MAX_ISOS, dtype=torch.float32, device=self.device)
+            d_offs = torch.zeros(MAX_ISOS + 1, dtype=torch.int64, device=self.device)
         h_offs = torch.zeros(MAX_ISOS + 1, dtype=torch.int64).pin_memory()
         h_isos = torch.empty(MAX_ISOS, dtype=torch.float32).pin_memory()
         while True:
@@ -194,7 +205,11 @@ class Server:
                     self.cv.wait(0.005)
                 if self.stop_flag and not batch:
                     return
-                res, fresh = self._admit(batch[0].dataset)
+                res, fresh, evicted = self._admit(batch[0].dataset)
+            if evicted:
+                with self.cuda_lock:
+                    for ctx in evicted:
+                        ctx.close()
             t0 = time.perf_counter()
             for r in batch:
                 r.t_start = t0
@@ -203,9 +218,15 @@ class Server:
                     if fresh:
                         self._prefill(res, stream)
                     out = self._serve(w, res, batch, stream, out, d_isos, d_offs, h_offs, h_isos)
-            except Exception as e:  # report per request, keep serving
+            except Exception:  # report per request, keep serving
+                err = traceback.format_exc()
                 for r in batch:
-                    r.error = repr(e)
+                    r.error = err
+                if res.ctx is None:                 # failed dual-mesh pass: forget the entry
+                    with self.cv:
+                        if self.resident.get(res.name) is res:
+                            self.resident.pop(res.name)
+                            self.used -= res.bytes
             t1 = time.perf_counter()
             for r in batch:
                 r.t_done = t1
@@ -217,10 +238,15 @@ class Server:
 
     def _prefill(self, res: _Resident, stream):
         ds = self.datasets[res.name]
-        ctx = amriso.AmrContext(self.device, stream)
-        ctx.upload(ds.xyz, ds.lvl, ds.s)
-        ctx.build_locator(**ds.opts)
-        ctx.dual_cells()
+        with self.cuda_lock:   # allocates device buffers
+            ctx = amriso.AmrContext(self.device, stream)
+            try:
+                ctx.upload(ds.xyz, ds.lvl, ds.s)
+                ctx.build_locator(**ds.opts)
+                ctx.dual_cells()
+            except Exception:
+                ctx.close()
+                raise
         real = ctx.info().device_bytes
         with self.cv:
             self.used += real - res.bytes
@@ -252,7 +278,9 @@ class Server:
         stream.synchronize()
         offs = h_offs[:bucket + 1].tolist()
         if offs[bucket] > out.shape[0]:     # buffer too small: grow, drop stale graphs, rerun
-            out = torch.empty((int(offs[bucket] * 1.25) + 1, 3, 3), dtype=torch.float32, device=self.device)
+            with self.cuda_lock:
+                out = torch.empty((int(offs[bucket] * 1.25) + 1, 3, 3), dtype=torch.float32,
+                                  device=self.device)
             res.graphs.clear()
             ctx.iso_batch_async(d_isos[:bucket], out, d_offs[:bucket + 1])
             h_offs[:bucket + 1].copy_(d_offs[:bucket + 1], non_blocking=True)
@@ -270,8 +298,9 @@ class Server:
         """CUDA graph of the batched step (count, device offsets, emit)."""
         stream.synchronize()
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
-            ctx.iso_batch_async(d_isos, out, d_offs)
+        with self.cuda_lock:
+            with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                ctx.iso_batch_async(d_isos, out, d_offs)
         return g
 
 

@@ -70,18 +70,18 @@ def test_lru_eviction_under_budget():
     try:
         for name in ("a", "b"):
             with srv.cv:
-                res, fresh = srv._admit(name)
-            assert fresh
+                res, fresh, ev = srv._admit(name)
+            assert fresh and not ev
             res.ctx = _FakeCtx()
             res.users = 0
         with srv.cv:                              # touch a: b becomes least recent
-            res, fresh = srv._admit("a")
+            res, fresh, ev = srv._admit("a")
         assert not fresh
         res.users = 0
         victim_ctx = srv.resident["b"].ctx
         with srv.cv:
-            res, fresh = srv._admit("c")          # 1200 > 1000: evict b
-        assert fresh and "b" not in srv.resident and victim_ctx.closed
+            res, fresh, ev = srv._admit("c")      # 1200 > 1000: evict b
+        assert fresh and "b" not in srv.resident and ev == [victim_ctx]
         assert srv.stats["evictions"] == 1 and srv.used == 800
     finally:
         serve.BYTES_PER_CELL_ESTIMATE = old
@@ -116,7 +116,8 @@ def test_mix_equals_alone():
     for r in reqs:
         assert r.done.wait(120)
     srv.stop()
-    assert all(r.error is None for r in reqs), [r.error for r in reqs if r.error]
+    errs = [r.error for r in reqs if r.error]
+    assert not errs, errs[0]
     assert srv.stats["prefills"] > len(data)          # the budget forced evictions
     assert srv.stats["graph_replays"] > 0
     assert any(r.batched_with > 1 for r in reqs)
