@@ -307,6 +307,10 @@ def run_serve(args):
                               "plain": run_plain(clone)}
     arr = np.cumsum(rng.exponential(1.0 / (0.8 * cap_plain), size=args.serve_requests))
     results["0.8_budget_8GB"] = {"server": run_server(make(args.serve_requests, arr), 8 << 30)}
+    # saturation: every request waiting at t = 0; throughput = triangles / makespan
+    reqs = make(args.serve_requests, np.zeros(args.serve_requests))
+    clone = [serve.Request(r.rid, r.dataset, list(r.isos), r.t_arrival) for r in reqs]
+    results["saturation"] = {"server": run_server(reqs, 120 << 30), "plain": run_plain(clone)}
     line = {"mode": "serve", "metric": METRIC, "unit": "ms (p50/p99 latency), triangles/s",
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "serving: 24 data sets 50k-50M cells (octree / block crops), Zipf(1), "

@@ -51,7 +51,8 @@ class AmrError(RuntimeError):
 
 class _LocatorOpts(ctypes.Structure):
     _fields_ = [("log2_brick", ctypes.c_int), ("load_factor", ctypes.c_float),
-                ("block_size", ctypes.c_int), ("check_overlap", ctypes.c_int)]
+                ("block_size", ctypes.c_int), ("check_overlap", ctypes.c_int),
+                ("partitioned", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -194,8 +195,11 @@ class AmrContext:
         self.n_dual = -1
 
     def build_locator(self, log2_brick: int = 3, load_factor: float = 0.5, block_size: int = 256,
-                      check_overlap: bool = False):
-        o = _LocatorOpts(int(log2_brick), float(load_factor), int(block_size), int(check_overlap))
+                      check_overlap: bool = False, partitioned: int = 0):
+        """partitioned: 0 by input size, 1 always bin cells before placing
+        them in their slots, -1 never."""
+        o = _LocatorOpts(int(log2_brick), float(load_factor), int(block_size), int(check_overlap),
+                         int(partitioned))
         rc = _lib.amr_build_locator(self._h, ctypes.byref(o))
         self._keep = None
         _check(rc, "amr_build_locator")

@@ -23,11 +23,12 @@ struct DevBuf {
 
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
-  KT_GET_DUALS, KT_NEIGHBORS, KT_COUNT
+  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN_PLACE, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
-    "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors"};
+    "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
+    "k_bin_place_cells"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -72,7 +73,7 @@ struct amr_ctx {
   float alpha = 0.5f;
   int block = 256;
   int check_overlap = 0;
-  DevBuf hkeys, hvals, bricks, rec, scal, view, nbr;
+  DevBuf hkeys, hvals, bricks, rec, scal, view, nbr, staging, bins;
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
   int levels = 0;
@@ -93,6 +94,10 @@ struct amr_ctx {
 };
 
 namespace {
+
+// Cell count from which the locator uses the partitioned scatter (smaller
+// sets fit L2 and scatter directly).
+constexpr long long kBinThreshold = 1ll << 24;
 
 size_t held(const DevBuf& b) { return b.bytes; }
 
@@ -286,8 +291,8 @@ void amr_destroy(amr_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                    &c->rec, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch, &c->stage_buf,
-                    &c->iso_buf, &c->seg_buf};
+                    &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->bins, &c->duals, &c->scratch,
+                    &c->stage_buf, &c->iso_buf, &c->seg_buf};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
   for (auto& v : c->pending)
@@ -345,13 +350,14 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   if (!c) return AMR_ERR_INVALID_ARG;
   if (c->stage < 1) return AMR_ERR_STATE;
   AMR_CUDA(cudaSetDevice(c->device));
-  int logb = 3, block = 256, overlap = 0;
+  int logb = 3, block = 256, overlap = 0, partitioned = 0;
   float alpha = 0.5f;
   if (opts) {
     if (opts->log2_brick) logb = opts->log2_brick;
     if (opts->load_factor > 0.f) alpha = opts->load_factor;
     if (opts->block_size) block = opts->block_size;
     overlap = opts->check_overlap;
+    partitioned = opts->partitioned;
   }
   if ((logb != 2 && logb != 3) || alpha < 0.05f || alpha > 0.9f || block < 32 || block > 1024 ||
       (block & 31))
@@ -412,7 +418,14 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   if (c->n_slots) {
     AMR_CUDA(cudaMemsetAsync(c->rec.p, 0xFF, (size_t)c->n_slots * 8, c->stream));
     const Locator L = make_locator(c);
-    {
+    if (partitioned > 0 || (partitioned == 0 && n >= kBinThreshold)) {   // partitioned scatter
+      AMR_TRY(ensure(c->staging, bin_staging_bytes(c->n_slots)));
+      AMR_TRY(ensure(c->bins, 512 * sizeof(unsigned long long)));
+      KernelTimer kt(c, KT_BIN_PLACE);
+      AMR_CUDA(launch_bin_place(logb, c->xyz, c->lvl, c->s, n, L, c->n_slots, static_cast<uint4*>(c->staging.p),
+                                static_cast<unsigned long long*>(c->bins.p),
+                                static_cast<unsigned long long*>(c->rec.p), dev_sc(c), c->sm_count, c->stream));
+    } else {
       KernelTimer kt(c, KT_SCATTER);
       AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, L,
                                     static_cast<unsigned long long*>(c->rec.p), dev_sc(c),
@@ -628,8 +641,8 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->n_levels = c->stage >= 2 ? c->levels : 0;
   info->log2_brick = c->logb;
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                          &c->rec, &c->scal, &c->view, &c->nbr, &c->duals, &c->scratch,
-                          &c->stage_buf, &c->iso_buf, &c->seg_buf};
+                          &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->bins, &c->duals,
+                          &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);
   info->device_bytes = total;

@@ -296,6 +296,85 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
   if (lane == 0 && err) atomicOr(&sc->err, err);
 }
 
+// Partitioned form of pass 2, for large inputs: the random slot writes of
+// k_scatter_cells leave L2 as partial sectors (a read-modify-write each in
+// DRAM). Instead, k_bin_cells bins the cells by slot range (2^kBinShift slots,
+// 32 MB of records, per bin) into a staging array, writing each CTA tile's
+// cells of one bin as one contiguous run; k_place_cells then streams the
+// staging array in order, so its random record writes fall into one or two
+// bins' windows at a time and are merged in L2.
+constexpr int kBinShift = 22;
+constexpr int kMaxBins = 1 << (31 - kBinShift);   // slot indices stay below 2^31
+constexpr int kBinThreads = 256;
+constexpr int kBinPerThread = 16;
+constexpr int kBinTile = kBinThreads * kBinPerThread;
+
+template <int LOGB>
+__global__ void __launch_bounds__(kBinThreads) k_bin_cells(
+    const int* __restrict__ xyz, const unsigned char* __restrict__ lvl, const float* __restrict__ s,
+    long long n, Locator L, uint4* __restrict__ staging, unsigned long long* __restrict__ bin_count,
+    int n_bins, Scratch* sc) {
+  __shared__ unsigned hist[kMaxBins];
+  __shared__ unsigned long long base[kMaxBins];
+  const int t = threadIdx.x;
+  unsigned err = 0;
+  for (long long tile0 = (long long)blockIdx.x * kBinTile; tile0 < n; tile0 += (long long)gridDim.x * kBinTile) {
+    for (int b = t; b < n_bins; b += kBinThreads) hist[b] = 0;
+    __syncthreads();
+    unsigned slot[kBinPerThread], rank[kBinPerThread];
+#pragma unroll
+    for (int j = 0; j < kBinPerThread; ++j) {
+      const long long i = tile0 + j * kBinThreads + t;
+      slot[j] = kReject;
+      rank[j] = 0;
+      if (i >= n) continue;
+      const int x = __ldg(xyz + 3 * i), y = __ldg(xyz + 3 * i + 1), z = __ldg(xyz + 3 * i + 2);
+      const int l = __ldg(lvl + i);
+      if (l > kMaxLevel) continue;
+      const int bi = find_brick(L, brick_key<LOGB>(x, y, z, l));
+      if (bi < 0) {
+        err |= ERR_HASH_FULL;
+        continue;
+      }
+      slot[j] = ((unsigned)bi << (3 * LOGB)) | local_index<LOGB>(x, y, z, l);
+      rank[j] = atomicAdd(&hist[slot[j] >> kBinShift], 1u);
+    }
+    __syncthreads();
+    for (int b = t; b < n_bins; b += kBinThreads)
+      if (hist[b]) base[b] = atomicAdd(bin_count + b, (unsigned long long)hist[b]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kBinPerThread; ++j) {
+      if (slot[j] == kReject) continue;
+      const long long i = tile0 + j * kBinThreads + t;
+      const unsigned b = slot[j] >> kBinShift;
+      const unsigned long long r = base[b] + rank[j];
+      if (r >= (1ull << kBinShift)) {   // more cells than slots in the bin: duplicates
+        err |= ERR_DUPLICATE;
+        continue;
+      }
+      staging[((long long)b << kBinShift) + (long long)r] =
+          make_uint4(slot[j], (unsigned)i, __float_as_uint(__ldg(s + i)), 0u);
+    }
+    __syncthreads();
+  }
+  err = warp_or(err);
+  if ((t & 31) == 0 && err) atomicOr(&sc->err, err);
+}
+
+__global__ void __launch_bounds__(256) k_place_cells(const uint4* __restrict__ staging,
+                                                     const unsigned long long* __restrict__ bin_count,
+                                                     long long n_slots, unsigned long long* __restrict__ rec) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x; pos < n_slots; pos += stride) {
+    const long long b = pos >> kBinShift;
+    const unsigned long long cnt = min(__ldg(bin_count + b), 1ull << kBinShift);   // written entries
+    if ((unsigned long long)(pos & ((1ll << kBinShift) - 1)) >= cnt) continue;
+    const uint4 e = __ldg(staging + pos);
+    rec[e.x] = ((unsigned long long)e.z << 32) | e.y;
+  }
+}
+
 // Pass over the slots: resolve every logical cell of every brick to the
 // actual cell containing it - its own occupant, else the first occupied slot
 // at a coarser level, else kReject (finer cells or a hole). With
@@ -943,6 +1022,29 @@ cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* 
                                  int grid, int block, cudaStream_t st) {
   AMR_DISPATCH(logb, (k_scatter_cells<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, loc, rec, sc)));
   return cudaGetLastError();
+}
+
+cudaError_t launch_bin_place(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
+                             Locator loc, long long n_slots, uint4* staging, unsigned long long* bin_count,
+                             unsigned long long* rec, Scratch* sc, int sm_count, cudaStream_t st) {
+  const int n_bins = (int)((n_slots + (1ll << kBinShift) - 1) >> kBinShift);
+  if (n <= 0 || n_bins <= 0) return cudaSuccess;
+  if (n_bins > kMaxBins) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(unsigned long long) * n_bins, st);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (n + kBinTile - 1) / kBinTile;
+  const int grid = (int)(tiles < (long long)sm_count * 8 ? tiles : (long long)sm_count * 8);
+  AMR_DISPATCH(logb, (k_bin_cells<LB><<<grid, kBinThreads, 0, st>>>(xyz, lvl, s, n, loc, staging, bin_count,
+                                                                     n_bins, sc)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_place_cells<<<sm_count * 8, 256, 0, st>>>(staging, bin_count, n_slots, rec);
+  return cudaGetLastError();
+}
+
+size_t bin_staging_bytes(long long n_slots) {
+  const long long n_bins = (n_slots + (1ll << kBinShift) - 1) >> kBinShift;
+  return (size_t)(n_bins << kBinShift) * sizeof(uint4);
 }
 
 cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, float* scal, long long n_slots,

@@ -159,6 +159,9 @@ class Server:
         while True:
             res = self.resident.get(name)
             if res is not None:
+                if res.users > 0:          # another worker holds it (a context is
+                    self.cv.wait(0.005)    # single-threaded); its prefill may be running
+                    continue
                 res.users += 1
                 self.resident.move_to_end(name)
                 return res, False, evicted

@@ -8,14 +8,14 @@ import torch
 import oracle
 
 
-def run_gpu(xyz, lv, s, iso, log2_brick=3, check_overlap=False, host_upload=False):
+def run_gpu(xyz, lv, s, iso, log2_brick=3, check_overlap=False, host_upload=False, partitioned=0):
     from paper_2004_08475_b300 import amriso
     ctx = amriso.AmrContext()
     if host_upload:
         ctx.upload(xyz.cpu(), lv.cpu(), s.cpu())
     else:
         ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
-    ctx.build_locator(log2_brick=log2_brick, check_overlap=check_overlap)
+    ctx.build_locator(log2_brick=log2_brick, check_overlap=check_overlap, partitioned=partitioned)
     nd = ctx.dual_cells()
     duals = ctx.get_duals().cpu().numpy().astype(np.int64)
     cases, ntri = ctx.iso_cases(iso)

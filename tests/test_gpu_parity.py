@@ -27,6 +27,33 @@ def test_sphere_tiny(logb):
     assert r["bit_exact_frac"] == 1.0
 
 
+@pytest.mark.parametrize("part", [-1, 1])
+def test_partitioned_placement(part):
+    """Both cell-placement paths of the locator build give the oracle's
+    result (the binned one is otherwise used from 2^24 cells on)."""
+    for seed in range(6):
+        gen = synth.random_octree(200 + seed, levels=2 + seed % 4, roots=5 if seed % 4 < 3 else 3,
+                                  p_split=0.45, p_hole=0.06, field="random" if seed % 2 else "sphere")
+        xyz, lv, s, iso, info = gen
+        g = run_gpu(xyz, lv, s, iso, log2_brick=2 + seed % 2, partitioned=part)
+        o = run_oracle(xyz, lv, s, iso)
+        compare(g, o, _extent(info))
+    xyz, lv, s, iso, info = synth.octree_gaussians(seed=12, roots=6, root_level=4)
+    compare(run_gpu(xyz, lv, s, iso, partitioned=part), run_oracle(xyz, lv, s, iso), _extent(info))
+
+
+def test_partitioned_duplicate_detected():
+    from paper_2004_08475_b300 import amriso
+    xyz = torch.tensor([[0, 0, 0], [2, 0, 0], [2, 0, 0]], dtype=torch.int32)
+    lv = torch.tensor([1, 1, 1], dtype=torch.uint8)
+    s = torch.tensor([0.0, 1.0, 2.0])
+    ctx = amriso.AmrContext()
+    ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+    with pytest.raises(amriso.AmrError) as e:
+        ctx.build_locator(partitioned=1)
+    assert e.value.code == amriso.ERR_DUPLICATE
+
+
 @pytest.mark.parametrize("seed", range(24))
 def test_random_octrees(seed):
     levels = 2 + seed % 4
