@@ -52,6 +52,8 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int) -> fl
     return {
         "k_insert_bricks": 17.0 * n,                 # xyz + level + scalar
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
+        "k_bin_cells": 17.0 * n + 16.0 * n,          # read the cell, write a binned entry
+        "k_place_cells": 16.0 * n + 8.0 * n,         # read the entry, write id + scalar
         "k_resolve_views": 8.0 * n_slots,            # read id, write view
         "k_dual_cells": 4.0 * n_slots + 32.0 * nd,   # read views once, write 8 slots / dual
         "k_mc": 32.0 * nd + 4.0 * n + 36.0 * nt,     # read tuples + scalars, write triangles
@@ -331,6 +333,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--log2-brick", type=int, default=3)
     ap.add_argument("--load-factor", type=float, default=0.5)
+    ap.add_argument("--partitioned", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -365,7 +368,7 @@ def main():
     n = info["n"]
     stream = torch.cuda.current_stream()
     ctx = amriso.AmrContext(local, stream)
-    opts = dict(log2_brick=args.log2_brick, load_factor=args.load_factor)
+    opts = dict(log2_brick=args.log2_brick, load_factor=args.load_factor, partitioned=args.partitioned)
 
     def step(tri_buf):
         ctx.upload(xyz, lv, s)
@@ -408,7 +411,8 @@ def main():
         nd_all, nt_all = float(nd), float(nt)
 
     kt = {k: v for k, v in ktimes.items() if v[1] > 0}
-    t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_resolve_views")) / args.steps
+    t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_bin_cells", "k_place_cells",
+                                               "k_resolve_views", "k_brick_neighbors")) / args.steps
     t_dual = kt.get("k_dual_cells", (0, 1))[0] / args.steps
     t_iso = kt.get("k_mc", (0, 1))[0] / args.steps
     launches = int(sum(v[1] for v in kt.values()))

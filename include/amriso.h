@@ -61,8 +61,8 @@ typedef struct amr_locator_opts {
   float load_factor;    /* target fill of the brick hash table, 0.05-0.9 [0.5] */
   int   block_size;     /* threads per block of cell-parallel kernels   [256] */
   int   check_overlap;  /* nonzero: reject cells inside coarser cells     [0] */
-  int   partitioned;    /* cell placement: 0 partitioned from 2^24 cells on,
-                           1 always partitioned, -1 never               [0] */
+  int   partitioned;    /* cell placement: > 0 bin cells by slot range first,
+                           else scatter them directly                   [0] */
 } amr_locator_opts;
 
 /* ---- context ------------------------------------------------------------ */

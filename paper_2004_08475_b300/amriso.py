@@ -196,8 +196,8 @@ class AmrContext:
 
     def build_locator(self, log2_brick: int = 3, load_factor: float = 0.5, block_size: int = 256,
                       check_overlap: bool = False, partitioned: int = 0):
-        """partitioned: 0 by input size, 1 always bin cells before placing
-        them in their slots, -1 never."""
+        """partitioned: 1 bins cells by slot range before placing them in
+        their slots; 0 or -1 scatters them directly."""
         o = _LocatorOpts(int(log2_brick), float(load_factor), int(block_size), int(check_overlap),
                          int(partitioned))
         rc = _lib.amr_build_locator(self._h, ctypes.byref(o))

@@ -23,12 +23,12 @@ struct DevBuf {
 
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
-  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN_PLACE, KT_COUNT
+  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
     "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
-    "k_bin_place_cells"};
+    "k_bin_cells", "k_place_cells"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -94,10 +94,6 @@ struct amr_ctx {
 };
 
 namespace {
-
-// Cell count from which the locator uses the partitioned scatter (smaller
-// sets fit L2 and scatter directly).
-constexpr long long kBinThreshold = 1ll << 24;
 
 size_t held(const DevBuf& b) { return b.bytes; }
 
@@ -418,13 +414,19 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   if (c->n_slots) {
     AMR_CUDA(cudaMemsetAsync(c->rec.p, 0xFF, (size_t)c->n_slots * 8, c->stream));
     const Locator L = make_locator(c);
-    if (partitioned > 0 || (partitioned == 0 && n >= kBinThreshold)) {   // partitioned scatter
+    if (partitioned > 0) {   // partitioned scatter
       AMR_TRY(ensure(c->staging, bin_staging_bytes(c->n_slots)));
       AMR_TRY(ensure(c->bins, 512 * sizeof(unsigned long long)));
-      KernelTimer kt(c, KT_BIN_PLACE);
-      AMR_CUDA(launch_bin_place(logb, c->xyz, c->lvl, c->s, n, L, c->n_slots, static_cast<uint4*>(c->staging.p),
-                                static_cast<unsigned long long*>(c->bins.p),
-                                static_cast<unsigned long long*>(c->rec.p), dev_sc(c), c->sm_count, c->stream));
+      {
+        KernelTimer kt(c, KT_BIN);
+        AMR_CUDA(launch_bin(logb, c->xyz, c->lvl, c->s, n, L, c->n_slots, static_cast<uint4*>(c->staging.p),
+                            static_cast<unsigned long long*>(c->bins.p),
+                            static_cast<unsigned long long*>(c->rec.p), dev_sc(c), c->sm_count, c->stream));
+      }
+      KernelTimer kt(c, KT_PLACE);
+      AMR_CUDA(launch_place(c->n_slots, static_cast<const uint4*>(c->staging.p),
+                            static_cast<const unsigned long long*>(c->bins.p),
+                            static_cast<unsigned long long*>(c->rec.p), c->sm_count, c->stream));
     } else {
       KernelTimer kt(c, KT_SCATTER);
       AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, L,

@@ -1024,7 +1024,7 @@ cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_place(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
+cudaError_t launch_bin(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
                              Locator loc, long long n_slots, uint4* staging, unsigned long long* bin_count,
                              unsigned long long* rec, Scratch* sc, int sm_count, cudaStream_t st) {
   const int n_bins = (int)((n_slots + (1ll << kBinShift) - 1) >> kBinShift);
@@ -1036,8 +1036,12 @@ cudaError_t launch_bin_place(int logb, const int* xyz, const unsigned char* lvl,
   const int grid = (int)(tiles < (long long)sm_count * 8 ? tiles : (long long)sm_count * 8);
   AMR_DISPATCH(logb, (k_bin_cells<LB><<<grid, kBinThreads, 0, st>>>(xyz, lvl, s, n, loc, staging, bin_count,
                                                                      n_bins, sc)));
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_place(long long n_slots, const uint4* staging, const unsigned long long* bin_count,
+                         unsigned long long* rec, int sm_count, cudaStream_t st) {
+  if (n_slots <= 0) return cudaSuccess;
   k_place_cells<<<sm_count * 8, 256, 0, st>>>(staging, bin_count, n_slots, rec);
   return cudaGetLastError();
 }

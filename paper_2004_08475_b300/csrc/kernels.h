@@ -75,9 +75,11 @@ cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* 
 
 // Partitioned scatter for large inputs (same result as launch_scatter_cells):
 // staging must hold bin_staging_bytes(n_slots) bytes, bin_count 512 counters.
-cudaError_t launch_bin_place(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
-                             Locator loc, long long n_slots, uint4* staging, unsigned long long* bin_count,
-                             unsigned long long* rec, Scratch* sc, int sm_count, cudaStream_t st);
+cudaError_t launch_bin(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
+                       Locator loc, long long n_slots, uint4* staging, unsigned long long* bin_count,
+                       unsigned long long* rec, Scratch* sc, int sm_count, cudaStream_t st);
+cudaError_t launch_place(long long n_slots, const uint4* staging, const unsigned long long* bin_count,
+                         unsigned long long* rec, int sm_count, cudaStream_t st);
 size_t bin_staging_bytes(long long n_slots);
 
 // Writes view[] and scal[] of every slot from rec[].

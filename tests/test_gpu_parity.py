@@ -29,8 +29,8 @@ def test_sphere_tiny(logb):
 
 @pytest.mark.parametrize("part", [-1, 1])
 def test_partitioned_placement(part):
-    """Both cell-placement paths of the locator build give the oracle's
-    result (the binned one is otherwise used from 2^24 cells on)."""
+    """Both cell-placement paths of the locator build (direct scatter and
+    binned by slot range) give the oracle's result."""
     for seed in range(6):
         gen = synth.random_octree(200 + seed, levels=2 + seed % 4, roots=5 if seed % 4 < 3 else 3,
                                   p_split=0.45, p_hole=0.06, field="random" if seed % 2 else "sphere")

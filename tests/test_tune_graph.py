@@ -28,7 +28,7 @@ def test_tune_sweep_records(tmp_path):
     r = tune.tune(x, l, s, iso, space={"log2_brick": (2, 3), "load_factor": (0.5,), "block_size": (256,)},
                   reps=1, path=p)
     assert r["best"]["log2_brick"] in (2, 3) and r["best_ms"] > 0 and len(r["table"]) == 2
-    assert tune.best_options(info["n"], info["levels"], path=p) == r["best"]
+    assert tune.best_options(info["n"], int(l.max()) + 1, path=p) == r["best"]
 
 
 @pytest.mark.gpu
