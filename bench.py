@@ -2,7 +2,9 @@
 """Benchmark of the AMR dual-mesh + iso-surface hot path on one B300.
 
 One step = the whole path over one data set resident in HBM:
-  amr_upload (device arrays) -> amr_build_locator -> amr_dual_cells -> amr_iso
+  amr_upload (device arrays) -> amr_build_locator -> amr_dual_cells_iso
+(the dual list is emitted, kept resident and contoured at the iso-value in
+one pass; --separate-iso runs amr_dual_cells then amr_iso instead).
 Prints one JSON line (rank 0). `value` = dual cells per second of step time;
 triangles/s, per-stage rates, the dominant kernel's roofline (live CUDA
 events, algorithmic bytes / launch time / measured HBM copy peak), an
@@ -57,6 +59,8 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int) -> fl
         "k_resolve_views": 8.0 * n_slots,            # read id, write view
         "k_dual_cells": 4.0 * n_slots + 32.0 * nd,   # read views once, write 8 slots / dual
         "k_mc": 32.0 * nd + 4.0 * n + 36.0 * nt,     # read tuples + scalars, write triangles
+        # read views + scalars once, write the dual list and the triangles
+        "k_dual_cells_iso": 8.0 * n_slots + 32.0 * nd + 36.0 * nt,
     }.get(kernel, 0.0)
 
 
@@ -334,6 +338,8 @@ def main():
     ap.add_argument("--log2-brick", type=int, default=3)
     ap.add_argument("--load-factor", type=float, default=0.5)
     ap.add_argument("--partitioned", type=int, default=0)
+    ap.add_argument("--separate-iso", action="store_true",
+                    help="amr_dual_cells then amr_iso instead of the fused amr_dual_cells_iso")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -373,8 +379,11 @@ def main():
     def step(tri_buf):
         ctx.upload(xyz, lv, s)
         ctx.build_locator(**opts)
-        nd = ctx.dual_cells()
-        nt = ctx.iso_count(iso, tri_buf)
+        if args.separate_iso:
+            nd = ctx.dual_cells()
+            nt = ctx.iso_count(iso, tri_buf)
+        else:
+            nd, nt = ctx.dual_cells_iso(iso, tri_buf)
         return nd, nt
 
     # size the triangle buffer once (exact count), then warm up
@@ -413,7 +422,7 @@ def main():
     kt = {k: v for k, v in ktimes.items() if v[1] > 0}
     t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_bin_cells", "k_place_cells",
                                                "k_resolve_views", "k_brick_neighbors")) / args.steps
-    t_dual = kt.get("k_dual_cells", (0, 1))[0] / args.steps
+    t_dual = (kt.get("k_dual_cells", (0, 1))[0] + kt.get("k_dual_cells_iso", (0, 1))[0]) / args.steps
     t_iso = kt.get("k_mc", (0, 1))[0] / args.steps
     launches = int(sum(v[1] for v in kt.values()))
 
@@ -429,7 +438,7 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
     dk = kernels[dom]
     units = {"k_insert_bricks": n, "k_scatter_cells": n, "k_resolve_views": inf.n_slots,
-             "k_dual_cells": inf.n_slots, "k_mc": nd}.get(dom, n)
+             "k_dual_cells": inf.n_slots, "k_dual_cells_iso": inf.n_slots, "k_mc": nd}.get(dom, n)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": dk["gbs"] / peak, "peak_source": peak_src,
                 "traffic": ncu_traffic(dom, args.workload, units),
@@ -479,8 +488,11 @@ def main():
         def e2e_step():
             ectx.upload(hx, hl, hs)
             ectx.build_locator(**opts)
-            d = ectx.dual_cells()
-            t = ectx.iso_count(iso, hout)
+            if args.separate_iso:
+                d = ectx.dual_cells()
+                t = ectx.iso_count(iso, hout)
+            else:
+                d, t = ectx.dual_cells_iso(iso, hout)
             return d, t
         e2e_step()
         torch.cuda.synchronize()

@@ -108,6 +108,17 @@ int amr_build_locator(amr_ctx* ctx, const amr_locator_opts* opts);
  * *n_dual receives the number of dual cells. Synchronises the stream. */
 int amr_dual_cells(amr_ctx* ctx, int64_t* n_dual);
 
+/* amr_dual_cells and amr_iso(iso) in one pass over the locator: every dual
+ * cell is emitted into the resident list (exactly as amr_dual_cells) and
+ * Marching Cubes runs on it at once, from the cell scalars already staged for
+ * the dual's neighbourhood - the paper's single extraction kernel (Sec. 5.1,
+ * Sec. 5.2) with the dual list kept for later iso-values. Outputs as
+ * amr_dual_cells (*n_dual) and amr_iso (tris, *n_tris, AMR_ERR_CAPACITY with
+ * the exact count; the dual list is resident either way). Synchronises the
+ * stream. */
+int amr_dual_cells_iso(amr_ctx* ctx, float iso, float* tris, int64_t cap,
+                       int64_t* n_dual, int64_t* n_tris, int flags);
+
 /* Copies the resident dual cells as cell IDs: out[n_dual][8] int32, vertex
  * order e = ex + 2 ey + 4 ez (vertex e sits at the logical cell offset e
  * from the dual's lowest vertex). The order of the dual cells is unspecified

@@ -76,6 +76,7 @@ def _load() -> ctypes.CDLL:
         "amr_build_locator": (I, [P, ctypes.POINTER(_LocatorOpts)]),
         "amr_dual_cells": (I, [P, ctypes.POINTER(I64)]),
         "amr_get_duals": (I, [P, P, I64, I]),
+        "amr_dual_cells_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), I]),
         "amr_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), I]),
         "amr_iso_cases": (I, [P, F, P, P, I]),
         "amr_iso_batch": (I, [P, P, I, P, I64, P, I]),
@@ -102,7 +103,8 @@ _lib = _load()
 EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_build_locator",
            "amr_dual_cells", "amr_get_duals", "amr_iso", "amr_iso_cases", "amr_iso_batch",
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
-           "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async")
+           "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async",
+           "amr_dual_cells_iso")
 
 
 def lib() -> ctypes.CDLL:
@@ -209,6 +211,20 @@ class AmrContext:
         _check(_lib.amr_dual_cells(self._h, ctypes.byref(n)), "amr_dual_cells")
         self.n_dual = n.value
         return n.value
+
+    def dual_cells_iso(self, iso: float, out: torch.Tensor):
+        """Dual cells (kept resident) and the triangles at `iso` in one pass.
+        Returns (n_dual, n_tris); n_tris may exceed out.shape[0], in which case
+        the triangle output is partial (the dual list is complete)."""
+        nd = ctypes.c_int64(0)
+        nt = ctypes.c_int64(0)
+        flags = HOST_PTRS if not out.is_cuda else DEVICE_PTRS
+        rc = _lib.amr_dual_cells_iso(self._h, ctypes.c_float(iso), _ptr(out), int(out.shape[0]),
+                                     ctypes.byref(nd), ctypes.byref(nt), flags)
+        if rc not in (OK, ERR_CAPACITY):
+            _check(rc, "amr_dual_cells_iso")
+        self.n_dual = nd.value
+        return nd.value, nt.value
 
     def get_duals(self, out: torch.Tensor | None = None) -> torch.Tensor:
         """Resident dual cells as input cell IDs, int32 [D, 8]."""

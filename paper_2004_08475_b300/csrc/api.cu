@@ -23,12 +23,12 @@ struct DevBuf {
 
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
-  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_COUNT
+  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
     "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
-    "k_bin_cells", "k_place_cells"};
+    "k_bin_cells", "k_place_cells", "k_dual_cells_iso"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -481,6 +481,54 @@ int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
       return AMR_OK;
     }
     cap = nd;  // exact count known: grow and run again
+  }
+  return AMR_ERR_CUDA;
+}
+
+int amr_dual_cells_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t* n_dual, int64_t* n_tris,
+                       int flags) {
+  if (!c || !n_dual || !n_tris || cap < 0 || (cap > 0 && !tris)) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 2) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  float* dst = tris;
+  if ((flags & AMR_HOST_PTRS) && cap > 0) {
+    AMR_TRY(ensure(c->stage_buf, (size_t)cap * 36));
+    dst = static_cast<float*>(c->stage_buf.p);
+  }
+  long long dcap = std::max(c->dual_cap, c->n + c->n / 4 + 1024);
+  AMR_TRY(ensure(c->iso_buf, sizeof(float) * kMaxIso));
+  AMR_TRY(ensure(c->seg_buf, sizeof(long long) * (kMaxIso + 1)));
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    AMR_TRY(ensure(c->duals, (size_t)dcap * 32));
+    c->dual_cap = (long long)(c->duals.bytes / 32);
+    AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->n_dual, 0, sizeof(unsigned long long), c->stream));
+    AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->n_tri[0], 0, sizeof(unsigned long long), c->stream));
+    {
+      KernelTimer kt(c, KT_DUAL_ISO);
+      AMR_CUDA(launch_dual_cells_iso(c->logb, make_locator(c), static_cast<const int*>(c->nbr.p), c->n_bricks,
+                                     static_cast<uint4*>(c->duals.p), c->dual_cap, dev_sc(c), iso, dst, cap,
+                                     c->mc, c->stream));
+    }
+    AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_dual, &dev_sc(c)->n_dual, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+    AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], &dev_sc(c)->n_tri[0], sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+    AMR_CUDA(cudaStreamSynchronize(c->stream));
+    const long long nd = (long long)c->host_sc->n_dual;
+    if (nd > c->dual_cap) {
+      dcap = nd;   // exact count known: grow and run again
+      continue;
+    }
+    const long long nt = (long long)c->host_sc->n_tri[0];
+    c->n_dual = nd;
+    c->stage = 3;
+    *n_dual = nd;
+    *n_tris = nt;
+    if (flags & AMR_HOST_PTRS) {
+      AMR_TRY(deliver(c, tris, dst, (size_t)std::min<long long>(nt, cap) * 36, flags));
+      AMR_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return nt > cap ? AMR_ERR_CAPACITY : AMR_OK;
   }
   return AMR_ERR_CUDA;
 }

@@ -486,164 +486,6 @@ __host__ __device__ constexpr DualMasks make_dual_masks() {
 
 __constant__ DualMasks c_masks = make_dual_masks();
 
-// Threads of the dual-cell CTA: one per brick slot up to 256, so that eight
-// CTAs fit an SM at B = 8 (each thread then owns two cells).
-template <int LOGB>
-struct DualShape {
-  static constexpr int kCells = 1 << (3 * LOGB);
-  static constexpr int kThreads = kCells < 256 ? kCells : 256;
-  static constexpr int kPerThread = kCells / kThreads;
-};
-
-// One CTA per brick. The CTA loads the brick's resolved views plus a
-// one-cell halo ((B+2)^3 entries, from the 26 neighbouring bricks of the same
-// level or the first coarser brick that covers them) into shared memory,
-// marking same-level cells in bit 31, and condenses every row of the region
-// into a mask (bit x: a cell exists, bit 16+x: it is of this brick's level).
-// Each cell then reads 9 row masks and decides its 8 duals: a dual is emitted
-// iff every vertex exists (rule 1), none is finer (rule 2: finer regions
-// resolve to kReject) and every same-level vertex comes after the cell in
-// (z,y,x) order (rule 3). Survivors are compacted with one atomic per CTA.
-template <int LOGB>
-__global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
-    Locator L, const int* __restrict__ nbr, long long n_bricks, uint4* __restrict__ duals, long long cap,
-    Scratch* sc) {
-  constexpr int B = 1 << LOGB;
-  constexpr int R = B + 2;
-  constexpr int NT = DualShape<LOGB>::kThreads;
-  constexpr int CPT = DualShape<LOGB>::kPerThread;
-  constexpr int NR = R * R * R;
-  constexpr int NW = (NT + 31) / 32;
-  constexpr unsigned kSame = 0x80000000u;   // slot indices stay below 2^31
-  __shared__ unsigned rv[NR];
-  __shared__ unsigned rmask[R * R];
-  __shared__ int nb[27];
-  __shared__ unsigned wsum[NW + 1];
-  __shared__ unsigned long long cta_base;
-  const int t = threadIdx.x;
-  const int lane = t & 31, wp = t >> 5;
-  int c0[CPT], px[CPT], py[CPT], pz[CPT];
-#pragma unroll
-  for (int j = 0; j < CPT; ++j) {
-    const int m = t + j * NT;   // Morton index of the cell inside the brick
-    px[j] = compact<LOGB>(m);
-    py[j] = compact<LOGB>(m >> 1);
-    pz[j] = compact<LOGB>(m >> 2);
-    c0[j] = px[j] + R * (py[j] + R * pz[j]);   // neighbourhood origin (cell - 1)
-  }
-  for (long long bi = blockIdx.x; bi < n_bricks; bi += gridDim.x) {
-    const int4 b = __ldg(L.bricks + bi);
-    const int l = b.w;
-    if (t < 27) nb[t] = __ldg(nbr + bi * 27 + t);
-    bool mine[CPT];
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {   // the brick itself: coalesced reads
-      const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)(t + j * NT);
-      const unsigned v = __ldg(L.view + s2);
-      mine[j] = v == s2;
-      rv[c0[j] + 1 + R + R * R] = mine[j] ? (v | kSame) : v;
-    }
-    __syncthreads();
-    for (int r = t; r < NR; r += NT) {   // the one-cell halo
-      const int rx = r % R, ry = (r / R) % R, rz = r / (R * R);
-      if (rx >= 1 && rx <= B && ry >= 1 && ry <= B && rz >= 1 && rz <= B) continue;
-      const int nbi = (rx == 0 ? 0 : (rx == R - 1 ? 2 : 1)) + 3 * (ry == 0 ? 0 : (ry == R - 1 ? 2 : 1)) +
-                      9 * (rz == 0 ? 0 : (rz == R - 1 ? 2 : 1));
-      const int e = nb[nbi];
-      unsigned v = kReject;
-      if (e >= 0) {
-        const int fb = e & ((1 << 27) - 1), lv = e >> 27;
-        const int x = b.x + ((rx - 1) << l), y = b.y + ((ry - 1) << l), z = b.z + ((rz - 1) << l);
-        const unsigned s2 = ((unsigned)fb << (3 * LOGB)) | local_index<LOGB>(x, y, z, lv);
-        v = __ldg(L.view + s2);
-        if (lv == l && v == s2) v |= kSame;
-      }
-      rv[r] = v;
-    }
-    __syncthreads();
-    for (int row = t; row < R * R; row += NT) {
-      unsigned m = 0;
-#pragma unroll
-      for (int rx = 0; rx < R; ++rx) {
-        const unsigned v = rv[row * R + rx];
-        if (v != kReject) m |= (1u << rx) | ((v >> 31) << (16 + rx));
-      }
-      rmask[row] = m;
-    }
-    __syncthreads();
-    unsigned emit[CPT];
-    unsigned cnt = 0;   // per-thread dual count of cell j in bits 16j..16j+15
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-      emit[j] = 0;
-      if (!mine[j]) continue;   // the slot holds no level-l cell
-      unsigned exist = 0, samem = 0;
-#pragma unroll
-      for (int oz = 0; oz < 3; ++oz)
-#pragma unroll
-        for (int oy = 0; oy < 3; ++oy) {
-          const unsigned m = rmask[(py[j] + oy) + R * (pz[j] + oz)];
-          const int sh = 3 * oy + 9 * oz;
-          exist |= ((m >> px[j]) & 7u) << sh;
-          samem |= ((m >> (16 + px[j])) & 7u) << sh;
-        }
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        const bool ok = ((exist & c_masks.all[d]) == c_masks.all[d]) && !(samem & c_masks.lower[d]);
-        emit[j] |= (ok ? 1u : 0u) << d;
-      }
-      cnt += (unsigned)__popc(emit[j]) << (16 * j);
-    }
-    // CTA-wide exclusive scan of the packed counts: the duals of all cells
-    // t (first half) come before those of all cells t + NT, keeping the
-    // output in the brick's Morton order (totals stay below 2^16)
-    unsigned incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[wp] = incl;
-    __syncthreads();
-    if (t == 0) {
-      unsigned run = 0;
-      for (int w = 0; w < NW; ++w) {
-        const unsigned x = wsum[w];
-        wsum[w] = run;
-        run += x;
-      }
-      wsum[NW] = run;   // packed per-half totals
-      unsigned tot = 0;
-#pragma unroll
-      for (int j = 0; j < CPT; ++j) tot += (run >> (16 * j)) & 0xFFFFu;
-      cta_base = tot ? atomicAdd(&sc->n_dual, (unsigned long long)tot) : 0ull;
-    }
-    __syncthreads();
-    const unsigned excl = wsum[wp] + incl - cnt;
-    long long half_base = (long long)cta_base;
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-      long long idx = half_base + ((excl >> (16 * j)) & 0xFFFFu);
-      half_base += (wsum[NW] >> (16 * j)) & 0xFFFFu;
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        if (!((emit[j] >> d) & 1u)) continue;
-        const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
-        unsigned v[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          v[e] = rv[c0[j] + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2))] & ~kSame;
-        if (idx < cap) {
-          duals[2 * idx] = make_uint4(v[0], v[1], v[2], v[3]);
-          duals[2 * idx + 1] = make_uint4(v[4], v[5], v[6], v[7]);
-        }
-        ++idx;
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Marching Cubes on dual cells (Sec. 5, 5.1, 5.2)
 // ---------------------------------------------------------------------------
@@ -788,6 +630,221 @@ __device__ __forceinline__ int case_of(const unsigned v[8], float sv[8], const f
     cas |= (sv[e] > iso ? 1 : 0) << e;
   }
   return cas;
+}
+
+// Threads of the dual-cell CTA: one per brick slot up to 256, so that eight
+// CTAs fit an SM at B = 8 (each thread then owns two cells).
+template <int LOGB>
+struct DualShape {
+  static constexpr int kCells = 1 << (3 * LOGB);
+  static constexpr int kThreads = kCells < 256 ? kCells : 256;
+  static constexpr int kPerThread = kCells / kThreads;
+};
+
+// One CTA per brick. The CTA loads the brick's resolved views plus a
+// one-cell halo ((B+2)^3 entries, from the 26 neighbouring bricks of the same
+// level or the first coarser brick that covers them) into shared memory,
+// marking same-level cells in bit 31, and condenses every row of the region
+// into a mask (bit x: a cell exists, bit 16+x: it is of this brick's level).
+// Each cell then reads 9 row masks and decides its 8 duals: a dual is emitted
+// iff every vertex exists (rule 1), none is finer (rule 2: finer regions
+// resolve to kReject) and every same-level vertex comes after the cell in
+// (z,y,x) order (rule 3). Survivors are compacted with one atomic per CTA.
+//
+// With ISO, the same pass also runs Marching Cubes at `iso` on every dual it
+// emits (the first iso-value of a data set, fused as in the paper's single
+// extraction kernel): the region's scalars are staged in shared memory too,
+// and the kept triangles are appended with one atomic per warp - the same
+// triangles, bit for bit, as k_mc over the resident dual list.
+template <int LOGB, bool ISO>
+__global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
+    Locator L, const int* __restrict__ nbr, long long n_bricks, uint4* __restrict__ duals, long long cap,
+    Scratch* sc, float iso, float* __restrict__ tris, long long tri_cap, const __grid_constant__ McConst mc) {
+  constexpr int B = 1 << LOGB;
+  constexpr int R = B + 2;
+  constexpr int NT = DualShape<LOGB>::kThreads;
+  constexpr int CPT = DualShape<LOGB>::kPerThread;
+  constexpr int NR = R * R * R;
+  constexpr int NW = (NT + 31) / 32;
+  constexpr unsigned kSame = 0x80000000u;   // slot indices stay below 2^31
+  __shared__ unsigned rv[NR];
+  __shared__ unsigned rmask[R * R];
+  __shared__ int nb[27];
+  __shared__ unsigned wsum[NW + 1];
+  __shared__ unsigned long long cta_base;
+  __shared__ float rsc[ISO ? NR : 1];                 // scalars of the region's cells
+  __shared__ McShared msh;
+  __shared__ unsigned row_v[ISO ? NT * kRow : 1];
+  __shared__ float row_s[ISO ? NT * kRow : 1];
+  const int t = threadIdx.x;
+  const int lane = t & 31, wp = t >> 5;
+  if (ISO) {
+    load_mc(msh, mc);   // made visible by the first barrier below
+  }
+  int c0[CPT], px[CPT], py[CPT], pz[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int m = t + j * NT;   // Morton index of the cell inside the brick
+    px[j] = compact<LOGB>(m);
+    py[j] = compact<LOGB>(m >> 1);
+    pz[j] = compact<LOGB>(m >> 2);
+    c0[j] = px[j] + R * (py[j] + R * pz[j]);   // neighbourhood origin (cell - 1)
+  }
+  for (long long bi = blockIdx.x; bi < n_bricks; bi += gridDim.x) {
+    const int4 b = __ldg(L.bricks + bi);
+    const int l = b.w;
+    if (t < 27) nb[t] = __ldg(nbr + bi * 27 + t);
+    bool mine[CPT];
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {   // the brick itself: coalesced reads
+      const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)(t + j * NT);
+      const unsigned v = __ldg(L.view + s2);
+      mine[j] = v == s2;
+      rv[c0[j] + 1 + R + R * R] = mine[j] ? (v | kSame) : v;
+    }
+    __syncthreads();
+    for (int r = t; r < NR; r += NT) {   // the one-cell halo
+      const int rx = r % R, ry = (r / R) % R, rz = r / (R * R);
+      if (rx >= 1 && rx <= B && ry >= 1 && ry <= B && rz >= 1 && rz <= B) continue;
+      const int nbi = (rx == 0 ? 0 : (rx == R - 1 ? 2 : 1)) + 3 * (ry == 0 ? 0 : (ry == R - 1 ? 2 : 1)) +
+                      9 * (rz == 0 ? 0 : (rz == R - 1 ? 2 : 1));
+      const int e = nb[nbi];
+      unsigned v = kReject;
+      if (e >= 0) {
+        const int fb = e & ((1 << 27) - 1), lv = e >> 27;
+        const int x = b.x + ((rx - 1) << l), y = b.y + ((ry - 1) << l), z = b.z + ((rz - 1) << l);
+        const unsigned s2 = ((unsigned)fb << (3 * LOGB)) | local_index<LOGB>(x, y, z, lv);
+        v = __ldg(L.view + s2);
+        if (lv == l && v == s2) v |= kSame;
+      }
+      rv[r] = v;
+    }
+    __syncthreads();
+    for (int row = t; row < R * R; row += NT) {
+      unsigned m = 0;
+#pragma unroll
+      for (int rx = 0; rx < R; ++rx) {
+        const unsigned v = rv[row * R + rx];
+        if (v != kReject) m |= (1u << rx) | ((v >> 31) << (16 + rx));
+      }
+      rmask[row] = m;
+    }
+    if (ISO) {
+      for (int r = t; r < NR; r += NT) {
+        const unsigned v = rv[r];
+        rsc[r] = v != kReject ? __ldg(L.scal + (v & ~kSame)) : 0.f;
+      }
+    }
+    __syncthreads();
+    unsigned emit[CPT];
+    unsigned cnt = 0;   // per-thread dual count of cell j in bits 16j..16j+15
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      emit[j] = 0;
+      if (!mine[j]) continue;   // the slot holds no level-l cell
+      unsigned exist = 0, samem = 0;
+#pragma unroll
+      for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+          const unsigned m = rmask[(py[j] + oy) + R * (pz[j] + oz)];
+          const int sh = 3 * oy + 9 * oz;
+          exist |= ((m >> px[j]) & 7u) << sh;
+          samem |= ((m >> (16 + px[j])) & 7u) << sh;
+        }
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const bool ok = ((exist & c_masks.all[d]) == c_masks.all[d]) && !(samem & c_masks.lower[d]);
+        emit[j] |= (ok ? 1u : 0u) << d;
+      }
+      cnt += (unsigned)__popc(emit[j]) << (16 * j);
+    }
+    // CTA-wide exclusive scan of the packed counts: the duals of all cells
+    // t (first half) come before those of all cells t + NT, keeping the
+    // output in the brick's Morton order (totals stay below 2^16)
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wp] = incl;
+    __syncthreads();
+    if (t == 0) {
+      unsigned run = 0;
+      for (int w = 0; w < NW; ++w) {
+        const unsigned x = wsum[w];
+        wsum[w] = run;
+        run += x;
+      }
+      wsum[NW] = run;   // packed per-half totals
+      unsigned tot = 0;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) tot += (run >> (16 * j)) & 0xFFFFu;
+      cta_base = tot ? atomicAdd(&sc->n_dual, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    const unsigned excl = wsum[wp] + incl - cnt;
+    long long half_base = (long long)cta_base;
+    unsigned ntri = 0;   // ISO: kept triangles of this thread's duals
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      long long idx = half_base + ((excl >> (16 * j)) & 0xFFFFu);
+      half_base += (wsum[NW] >> (16 * j)) & 0xFFFFu;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        if (!((emit[j] >> d) & 1u)) continue;
+        const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+        unsigned v[8];
+        int cas = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int r = c0[j] + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2));
+          v[e] = rv[r] & ~kSame;
+          if (ISO) cas |= (rsc[r] > iso ? 1 : 0) << e;
+        }
+        if (idx < cap) {
+          duals[2 * idx] = make_uint4(v[0], v[1], v[2], v[3]);
+          duals[2 * idx + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+        }
+        ++idx;
+        if (ISO && msh.count[cas]) ntri += __popc(kept_triangles(msh.packed[cas], msh.count[cas], v, mc.edge_a,
+                                                                 mc.edge_b));
+      }
+    }
+    if (ISO) {   // append this warp's triangles, then write them
+      long long tidx = warp_append(ntri, &sc->n_tri[0]);
+      unsigned* vr = row_v + t * kRow;
+      float* sr = row_s + t * kRow;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        if (!ntri) break;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          if (!((emit[j] >> d) & 1u)) continue;
+          const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+          unsigned v[8];
+          float sv[8];
+          int cas = 0;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int r = c0[j] + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2));
+            v[e] = rv[r] & ~kSame;
+            sv[e] = rsc[r];
+            cas |= (sv[e] > iso ? 1 : 0) << e;
+          }
+          if (!msh.count[cas]) continue;
+          const unsigned keep = kept_triangles(msh.packed[cas], msh.count[cas], v, mc.edge_a, mc.edge_b);
+          if (!keep) continue;
+          stage_row(vr, sr, v, sv);
+          write_triangles<LOGB>(L.bricks, vr, sr, iso, msh.packed[cas], keep, tidx, tri_cap, tris, mc.edge_a,
+                                mc.edge_b);
+          tidx += __popc(keep);
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // One lane per dual, two duals per lane per step: gather the 8 vertex
@@ -1070,8 +1127,19 @@ cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, long long n
                               long long cap, Scratch* sc, cudaStream_t st) {
   if (n_bricks <= 0) return cudaSuccess;
   const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
-  AMR_DISPATCH(logb, (k_dual_cells<LB><<<grid, DualShape<LB>::kThreads, 0, st>>>(loc, nbr, n_bricks, duals,
-                                                                                 cap, sc)));
+  McConst none{};
+  AMR_DISPATCH(logb, (k_dual_cells<LB, false><<<grid, DualShape<LB>::kThreads, 0, st>>>(
+                         loc, nbr, n_bricks, duals, cap, sc, 0.f, nullptr, 0, none)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, long long n_bricks, uint4* duals,
+                                  long long cap, Scratch* sc, float iso, float* tris, long long tri_cap,
+                                  const McConst& mc, cudaStream_t st) {
+  if (n_bricks <= 0) return cudaSuccess;
+  const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
+  AMR_DISPATCH(logb, (k_dual_cells<LB, true><<<grid, DualShape<LB>::kThreads, 0, st>>>(
+                         loc, nbr, n_bricks, duals, cap, sc, iso, tris, tri_cap, mc)));
   return cudaGetLastError();
 }
 

@@ -42,6 +42,39 @@ def test_partitioned_placement(part):
     compare(run_gpu(xyz, lv, s, iso, partitioned=part), run_oracle(xyz, lv, s, iso), _extent(info))
 
 
+@pytest.mark.parametrize("case", range(8))
+def test_fused_dual_iso_equals_separate(case):
+    """amr_dual_cells_iso gives the same resident dual list and the same
+    triangles (bit for bit after canonical ordering) as amr_dual_cells
+    followed by amr_iso, and both match the oracle."""
+    from paper_2004_08475_b300 import amriso
+    if case < 5:
+        gen = synth.random_octree(300 + case, levels=2 + case % 4, roots=5, p_split=0.45, p_hole=0.06,
+                                  field="random" if case % 2 else "sphere")
+    elif case == 5:
+        gen = synth.sphere_tiny()
+    elif case == 6:
+        gen = synth.octree_gaussians(seed=12, roots=6, root_level=4)
+    else:
+        gen = synth.wing_bands(seed=14, dims=(24, 24, 8), bands=(3.0, 7.0, 14.0), iso=8.0)
+    xyz, lv, s, iso, info = gen
+    for logb in (2, 3):
+        ctx = amriso.AmrContext()
+        ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+        ctx.build_locator(log2_brick=logb)
+        out = torch.empty((200000, 3, 3), dtype=torch.float32, device="cuda")
+        nd, nt = ctx.dual_cells_iso(iso, out)
+        fused_tris = out[:nt].cpu().numpy()
+        fused_duals = ctx.get_duals().cpu().numpy().astype(np.int64)
+        cases, ntri = ctx.iso_cases(iso)
+        assert int(ntri.sum()) == nt
+        sep = ctx.iso(iso).cpu().numpy()
+        assert sep.shape[0] == nt
+        assert (canonical(fused_tris) == canonical(sep)).all()
+        g = {"duals": fused_duals, "cases": cases.cpu().numpy(), "ntri": ntri.cpu().numpy(), "tris": fused_tris}
+        compare(g, run_oracle(xyz, lv, s, iso), _extent(info))
+
+
 def test_partitioned_duplicate_detected():
     from paper_2004_08475_b300 import amriso
     xyz = torch.tensor([[0, 0, 0], [2, 0, 0], [2, 0, 0]], dtype=torch.int32)
