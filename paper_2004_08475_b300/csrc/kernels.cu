@@ -103,8 +103,9 @@ __device__ __forceinline__ unsigned warp_or(unsigned v) { return __reduce_or_syn
 
 constexpr int kUnroll = 4;   // cells per lane per trip of the cell-parallel loops
 
-// Pass 1 over the cells: validate, take the bounding box and the deepest
-// level, and insert every cell's brick key into the hash table. The CAS
+// Pass 1 over the cells: validate corners and levels, take the bounding box
+// and the deepest level, and insert every cell's brick key into the hash
+// table (scalars are checked in pass 2). The CAS
 // winner of a key numbers the brick and records its corner and level. Each
 // lane takes kUnroll cells per trip, loads and first probes hoisted, so that
 // their memory latencies overlap. Lanes holding the same key simply both
@@ -127,19 +128,16 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   for (long long base = wid * 32 * kUnroll; base < n; base += nwarps * 32 * kUnroll) {
     if ((trip++ & 31) == 0 && __any_sync(kFull, (__ldcg(&sc->err) & ERR_HASH_FULL) != 0u)) break;
     int x[kUnroll], y[kUnroll], z[kUnroll], l[kUnroll];
-    float v[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const long long i = base + u * 32 + lane;
       x[u] = y[u] = z[u] = 0;
       l[u] = -1;
-      v[u] = 0.f;
-      if (i < n) {
-        x[u] = __ldg(xyz + 3 * i);
-        y[u] = __ldg(xyz + 3 * i + 1);
-        z[u] = __ldg(xyz + 3 * i + 2);
-        l[u] = __ldg(lvl + i);
-        v[u] = __ldg(s + i);
+      if (i < n) {   // streamed once: evict first, keep the hash table in L2
+        x[u] = __ldcs(xyz + 3 * i);
+        y[u] = __ldcs(xyz + 3 * i + 1);
+        z[u] = __ldcs(xyz + 3 * i + 2);
+        l[u] = __ldcs(lvl + i);
       }
     }
     unsigned long long key[kUnroll], h[kUnroll], cur[kUnroll];
@@ -148,7 +146,6 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
     for (int u = 0; u < kUnroll; ++u) {
       key[u] = kEmptyKey;
       if (l[u] >= 0) {
-        if (!isfinite(v[u])) err |= ERR_NONFINITE;
         if (l[u] > kMaxLevel) {
           err |= ERR_RANGE;
         } else if ((x[u] | y[u] | z[u]) & ((1 << l[u]) - 1)) {
@@ -263,11 +260,12 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
       l[u] = -1;
       v[u] = 0.f;
       if (i < n) {
-        x[u] = __ldg(xyz + 3 * i);
-        y[u] = __ldg(xyz + 3 * i + 1);
-        z[u] = __ldg(xyz + 3 * i + 2);
-        l[u] = __ldg(lvl + i);
-        v[u] = __ldg(s + i);
+        x[u] = __ldcs(xyz + 3 * i);
+        y[u] = __ldcs(xyz + 3 * i + 1);
+        z[u] = __ldcs(xyz + 3 * i + 2);
+        l[u] = __ldcs(lvl + i);
+        v[u] = __ldcs(s + i);
+        if (!isfinite(v[u])) err |= ERR_NONFINITE;
       }
     }
     unsigned long long key[kUnroll], k0[kUnroll];
@@ -328,8 +326,9 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_cells(
       slot[j] = kReject;
       rank[j] = 0;
       if (i >= n) continue;
-      const int x = __ldg(xyz + 3 * i), y = __ldg(xyz + 3 * i + 1), z = __ldg(xyz + 3 * i + 2);
-      const int l = __ldg(lvl + i);
+      const int x = __ldcs(xyz + 3 * i), y = __ldcs(xyz + 3 * i + 1), z = __ldcs(xyz + 3 * i + 2);
+      const int l = __ldcs(lvl + i);
+      if (!isfinite(__ldg(s + i))) err |= ERR_NONFINITE;
       if (l > kMaxLevel) continue;
       const int bi = find_brick(L, brick_key<LOGB>(x, y, z, l));
       if (bi < 0) {
@@ -503,8 +502,8 @@ __device__ __forceinline__ void load_mc(McShared& sh, const McConst& mc) {
 }
 
 __device__ __forceinline__ void load_dual(const uint4* __restrict__ duals, long long d, unsigned v[8]) {
-  const uint4 a = __ldg(duals + 2 * d);
-  const uint4 c = __ldg(duals + 2 * d + 1);
+  const uint4 a = __ldcs(duals + 2 * d);   // streamed: keep the scalars in L2 instead
+  const uint4 c = __ldcs(duals + 2 * d + 1);
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
 }
@@ -803,9 +802,9 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
           v[e] = rv[r] & ~kSame;
           if (ISO) cas |= (rsc[r] > iso ? 1 : 0) << e;
         }
-        if (idx < cap) {
-          duals[2 * idx] = make_uint4(v[0], v[1], v[2], v[3]);
-          duals[2 * idx + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+        if (idx < cap) {   // written once, read much later: evict first
+          __stcs(duals + 2 * idx, make_uint4(v[0], v[1], v[2], v[3]));
+          __stcs(duals + 2 * idx + 1, make_uint4(v[4], v[5], v[6], v[7]));
         }
         ++idx;
         if (ISO && msh.count[cas]) ntri += __popc(kept_triangles(msh.packed[cas], msh.count[cas], v, mc.edge_a,
@@ -816,10 +815,10 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
       long long tidx = warp_append(ntri, &sc->n_tri[0]);
       unsigned* vr = row_v + t * kRow;
       float* sr = row_s + t * kRow;
-#pragma unroll
+#pragma unroll 1
       for (int j = 0; j < CPT; ++j) {
         if (!ntri) break;
-#pragma unroll
+#pragma unroll 1
         for (int d = 0; d < 8; ++d) {
           if (!((emit[j] >> d) & 1u)) continue;
           const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
