@@ -2,9 +2,8 @@
 """Benchmark of the AMR dual-mesh + iso-surface hot path on one B300.
 
 One step = the whole path over one data set resident in HBM:
-  amr_upload (device arrays) -> amr_build_locator -> amr_dual_cells_iso
-(the dual list is emitted, kept resident and contoured at the iso-value in
-one pass; --separate-iso runs amr_dual_cells then amr_iso instead).
+  amr_upload (device arrays) -> amr_build_locator -> amr_dual_cells -> amr_iso
+(--fused-iso uses amr_dual_cells_iso, the one-pass form, instead).
 Prints one JSON line (rank 0). `value` = dual cells per second of step time;
 triangles/s, per-stage rates, the dominant kernel's roofline (live CUDA
 events, algorithmic bytes / launch time / measured HBM copy peak), an
@@ -52,7 +51,7 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int) -> fl
     """Compulsory bytes per launch of each kernel under the library's data
     layout: what the kernel must read and write at least once."""
     return {
-        "k_insert_bricks": 17.0 * n,                 # xyz + level + scalar
+        "k_insert_bricks": 13.0 * n,                 # xyz + level
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
         "k_bin_cells": 17.0 * n + 16.0 * n,          # read the cell, write a binned entry
         "k_place_cells": 16.0 * n + 8.0 * n,         # read the entry, write id + scalar
@@ -338,8 +337,8 @@ def main():
     ap.add_argument("--log2-brick", type=int, default=3)
     ap.add_argument("--load-factor", type=float, default=0.5)
     ap.add_argument("--partitioned", type=int, default=0)
-    ap.add_argument("--separate-iso", action="store_true",
-                    help="amr_dual_cells then amr_iso instead of the fused amr_dual_cells_iso")
+    ap.add_argument("--fused-iso", action="store_true",
+                    help="amr_dual_cells_iso (one pass) instead of amr_dual_cells then amr_iso")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -379,7 +378,7 @@ def main():
     def step(tri_buf):
         ctx.upload(xyz, lv, s)
         ctx.build_locator(**opts)
-        if args.separate_iso:
+        if not args.fused_iso:
             nd = ctx.dual_cells()
             nt = ctx.iso_count(iso, tri_buf)
         else:
@@ -488,7 +487,7 @@ def main():
         def e2e_step():
             ectx.upload(hx, hl, hs)
             ectx.build_locator(**opts)
-            if args.separate_iso:
+            if not args.fused_iso:
                 d = ectx.dual_cells()
                 t = ectx.iso_count(iso, hout)
             else:
@@ -531,6 +530,7 @@ def main():
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "n_cells": n,
+                       "step": "fused" if args.fused_iso else "dual_cells+iso",
                        "n_dual": nd, "n_triangles": nt, "iso": iso, "n_bricks": inf.n_bricks,
                        "n_slots": inf.n_slots, "levels": inf.n_levels, "log2_brick": args.log2_brick,
                        "load_factor": args.load_factor, "parallelism": f"replicas{world}",
