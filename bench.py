@@ -44,6 +44,10 @@ WORKLOADS = {
     "block": ("block_vortex: 8^3-cell blocks, widths 1-8, 4096x2048x2048, 5% holes, |curl| of "
               "vortex rings", lambda dev: synth.block_vortex(device=dev)),
     "sphere": ("sphere_tiny: 32^3, 2 levels, distance field, iso 8", lambda dev: synth.sphere_tiny(device=dev)),
+    # an eighth of the wing workload (inputs still far larger than L2): the
+    # stand-in on which ncu captures of the wing's kernels are taken
+    "wing_eighth": ("wing_bands at half the root grid per axis (profiling stand-in)",
+                    lambda dev: synth.wing_bands(device=dev, dims=(224, 224, 48), scale=0.5)),
 }
 
 

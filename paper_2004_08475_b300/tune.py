@@ -107,3 +107,21 @@ def tune(xyz, lvl, s, iso: float, space: dict | None = None, reps: int = 3, path
         cache[bucket_key(int(xyz.shape[0]), lv, torch.cuda.get_device_name())] = result
         save_cache(cache, path)
     return result
+
+
+def _main():
+    import argparse
+    from . import synth
+    ap = argparse.ArgumentParser(description="tune the locator options on a synthetic workload")
+    ap.add_argument("--workload", default="octree", choices=["octree", "block", "wing", "sphere"])
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    gen = {"octree": synth.octree_gaussians, "block": synth.block_vortex, "wing": synth.wing_bands,
+           "sphere": synth.sphere_tiny}[args.workload]
+    x, l, s, iso, info = gen(device="cuda")
+    r = tune(x, l, s, iso, reps=args.reps)
+    print(json.dumps({"workload": args.workload, "n": info["n"], **r}))
+
+
+if __name__ == "__main__":
+    _main()
