@@ -59,7 +59,7 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int) -> fl
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
         "k_bin_cells": 17.0 * n + 16.0 * n,          # read the cell, write a binned entry
         "k_place_cells": 16.0 * n + 8.0 * n,         # read the entry, write id + scalar
-        "k_resolve_views": 8.0 * n_slots,            # read id, write view
+        "k_resolve_views": 16.0 * n_slots,           # read the record, write view + scalar
         "k_dual_cells": 4.0 * n_slots + 32.0 * nd,   # read views once, write 8 slots / dual
         "k_mc": 32.0 * nd + 4.0 * n + 36.0 * nt,     # read tuples + scalars, write triangles
         # read views + scalars once, write the dual list and the triangles
