@@ -57,8 +57,9 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int) -> fl
     return {
         "k_insert_bricks": 13.0 * n,                 # xyz + level
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
-        "k_bin_cells": 17.0 * n + 16.0 * n,          # read the cell, write a binned entry
-        "k_place_cells": 16.0 * n + 8.0 * n,         # read the entry, write id + scalar
+        "k_bin_coarse": 17.0 * n + 12.0 * n,         # read the cell, write a 12-byte entry
+        "k_bin_fine": 12.0 * n + 12.0 * n,           # re-split the entries by window
+        "k_place_windows": 12.0 * n + 8.0 * n_slots, # read the entries, write every slot's record
         "k_resolve_views": 16.0 * n_slots,           # read the record, write view + scalar
         "k_dual_cells": 4.0 * n_slots + 32.0 * nd,   # read views once, write 8 slots / dual
         "k_mc": 32.0 * nd + 4.0 * n + 36.0 * nt,     # read tuples + scalars, write triangles
@@ -423,8 +424,8 @@ def main():
         nd_all, nt_all = float(nd), float(nt)
 
     kt = {k: v for k, v in ktimes.items() if v[1] > 0}
-    t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_bin_cells", "k_place_cells",
-                                               "k_resolve_views", "k_brick_neighbors")) / args.steps
+    t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_bin_coarse", "k_bin_fine",
+                                               "k_place_windows", "k_resolve_views", "k_brick_neighbors")) / args.steps
     t_dual = (kt.get("k_dual_cells", (0, 1))[0] + kt.get("k_dual_cells_iso", (0, 1))[0]) / args.steps
     t_iso = kt.get("k_mc", (0, 1))[0] / args.steps
     launches = int(sum(v[1] for v in kt.values()))
@@ -440,7 +441,8 @@ def main():
                       "algorithmic_bytes": b, "gbs": b / per / 1e6 if per > 0 else 0.0}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
     dk = kernels[dom]
-    units = {"k_insert_bricks": n, "k_scatter_cells": n, "k_resolve_views": inf.n_slots,
+    units = {"k_insert_bricks": n, "k_scatter_cells": n, "k_bin_coarse": n, "k_bin_fine": n,
+             "k_place_windows": inf.n_slots, "k_resolve_views": inf.n_slots,
              "k_dual_cells": inf.n_slots, "k_dual_cells_iso": inf.n_slots, "k_mc": nd}.get(dom, n)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": dk["gbs"] / peak, "peak_source": peak_src,

@@ -61,8 +61,10 @@ typedef struct amr_locator_opts {
   float load_factor;    /* target fill of the brick hash table, 0.05-0.9 [0.5] */
   int   block_size;     /* threads per block of cell-parallel kernels   [256] */
   int   check_overlap;  /* nonzero: reject cells inside coarser cells     [0] */
-  int   partitioned;    /* cell placement: > 0 bin cells by slot range first,
-                           else scatter them directly                   [0] */
+  int   partitioned;    /* cell placement: > 0 always binned (a two-level
+                           split by slot, then each window of slots built in
+                           shared memory and written whole), < 0 always a
+                           direct scatter, 0 binned from 2^20 cells on  [0] */
 } amr_locator_opts;
 
 /* ---- context ------------------------------------------------------------ */
@@ -176,6 +178,13 @@ int amr_iso_batch_async(amr_ctx* ctx, const float* d_isos, int n_iso,
 
 /* Waits for all work queued on the context's stream. */
 int amr_sync(amr_ctx* ctx);
+
+/* Frees the context's scratch workspace after waiting for its stream: the
+ * staging of the binned cell placement (24 bytes per slot) and of host-
+ * pointer delivery. The locator, the dual cells and the input stay; later
+ * calls re-create the workspace on demand. No counterpart in the paper: a
+ * memory-budget aid for keeping many data sets resident. */
+int amr_trim(amr_ctx* ctx);
 
 /* Human-readable text for a return code (static storage). */
 const char* amr_strerror(int code);

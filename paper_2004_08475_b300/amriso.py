@@ -82,6 +82,7 @@ def _load() -> ctypes.CDLL:
         "amr_iso_batch": (I, [P, P, I, P, I64, P, I]),
         "amr_iso_batch_async": (I, [P, P, I, P, I64, P]),
         "amr_sync": (I, [P]),
+        "amr_trim": (I, [P]),
         "amr_strerror": (ctypes.c_char_p, [I]),
         "amr_mc_table": (I, [P, P]),
         "amr_get_info": (I, [P, ctypes.POINTER(_Info)]),
@@ -104,7 +105,7 @@ EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_bui
            "amr_dual_cells", "amr_get_duals", "amr_iso", "amr_iso_cases", "amr_iso_batch",
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
            "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async",
-           "amr_dual_cells_iso")
+           "amr_dual_cells_iso", "amr_trim")
 
 
 def lib() -> ctypes.CDLL:
@@ -198,8 +199,9 @@ class AmrContext:
 
     def build_locator(self, log2_brick: int = 3, load_factor: float = 0.5, block_size: int = 256,
                       check_overlap: bool = False, partitioned: int = 0):
-        """partitioned: 1 bins cells by slot range before placing them in
-        their slots; 0 or -1 scatters them directly."""
+        """partitioned: 1 places the cells by the binned passes (split by
+        slot range, then each window of slots written whole), -1 by a direct
+        scatter, 0 binned from 2^20 cells on."""
         o = _LocatorOpts(int(log2_brick), float(load_factor), int(block_size), int(check_overlap),
                          int(partitioned))
         rc = _lib.amr_build_locator(self._h, ctypes.byref(o))
@@ -299,6 +301,11 @@ class AmrContext:
 
     def sync(self):
         _check(_lib.amr_sync(self._h), "amr_sync")
+
+    def trim(self):
+        """Free the scratch workspace (binned-placement and host-delivery
+        staging); the locator and dual cells stay resident."""
+        _check(_lib.amr_trim(self._h), "amr_trim")
 
     # -- introspection -----------------------------------------------------
     def info(self) -> Info:

@@ -16,6 +16,10 @@ using namespace amriso;
 
 namespace {
 
+// Inputs from this many cells on are placed by the binned passes (the direct
+// scatter is bound by one store transaction per cell).
+constexpr long long kBinnedMinCells = 1ll << 20;
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -23,12 +27,12 @@ struct DevBuf {
 
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
-  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_COUNT
+  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_BIN_FINE, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
     "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
-    "k_bin_cells", "k_place_cells", "k_dual_cells_iso"};
+    "k_bin_coarse", "k_place_windows", "k_dual_cells_iso", "k_bin_fine"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -73,7 +77,7 @@ struct amr_ctx {
   float alpha = 0.5f;
   int block = 256;
   int check_overlap = 0;
-  DevBuf hkeys, hvals, bricks, rec, scal, view, nbr, staging, bins;
+  DevBuf hkeys, hvals, bricks, rec, scal, view, nbr, staging;
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
   int levels = 0;
@@ -287,7 +291,7 @@ void amr_destroy(amr_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                    &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->bins, &c->duals, &c->scratch,
+                    &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->duals, &c->scratch,
                     &c->stage_buf, &c->iso_buf, &c->seg_buf};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
@@ -309,6 +313,15 @@ int amr_set_stream(amr_ctx* c, void* cuda_stream) {
 int amr_sync(amr_ctx* c) {
   if (!c) return AMR_ERR_INVALID_ARG;
   AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return AMR_OK;
+}
+
+int amr_trim(amr_ctx* c) {
+  if (!c) return AMR_ERR_INVALID_ARG;
+  AMR_CUDA(cudaSetDevice(c->device));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  release(c->staging);
+  release(c->stage_buf);
   return AMR_OK;
 }
 
@@ -412,22 +425,24 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   AMR_TRY(ensure(c->scal, (size_t)c->n_slots * 4));
   AMR_TRY(ensure(c->view, (size_t)c->n_slots * 4));
   if (c->n_slots) {
-    AMR_CUDA(cudaMemsetAsync(c->rec.p, 0xFF, (size_t)c->n_slots * 8, c->stream));
     const Locator L = make_locator(c);
-    if (partitioned > 0) {   // partitioned scatter
-      AMR_TRY(ensure(c->staging, bin_staging_bytes(c->n_slots)));
-      AMR_TRY(ensure(c->bins, 512 * sizeof(unsigned long long)));
+    // binned placement unless asked otherwise or the input is small
+    if (partitioned > 0 || (partitioned == 0 && n >= kBinnedMinCells)) {
+      AMR_TRY(ensure(c->staging, bin_layout(c->n_slots).bytes));
       {
         KernelTimer kt(c, KT_BIN);
-        AMR_CUDA(launch_bin(logb, c->xyz, c->lvl, c->s, n, L, c->n_slots, static_cast<uint4*>(c->staging.p),
-                            static_cast<unsigned long long*>(c->bins.p),
-                            static_cast<unsigned long long*>(c->rec.p), dev_sc(c), c->sm_count, c->stream));
+        AMR_CUDA(launch_bin_coarse(logb, c->xyz, c->lvl, c->s, n, L, c->n_slots, c->staging.p, dev_sc(c),
+                                   c->sm_count, c->stream));
+      }
+      {
+        KernelTimer kt(c, KT_BIN_FINE);
+        AMR_CUDA(launch_bin_fine(c->n_slots, c->staging.p, dev_sc(c), c->stream));
       }
       KernelTimer kt(c, KT_PLACE);
-      AMR_CUDA(launch_place(c->n_slots, static_cast<const uint4*>(c->staging.p),
-                            static_cast<const unsigned long long*>(c->bins.p),
-                            static_cast<unsigned long long*>(c->rec.p), c->sm_count, c->stream));
+      AMR_CUDA(launch_place_windows(c->n_slots, c->staging.p, static_cast<unsigned long long*>(c->rec.p),
+                                    c->stream));
     } else {
+      AMR_CUDA(cudaMemsetAsync(c->rec.p, 0xFF, (size_t)c->n_slots * 8, c->stream));
       KernelTimer kt(c, KT_SCATTER);
       AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, L,
                                     static_cast<unsigned long long*>(c->rec.p), dev_sc(c),
@@ -691,7 +706,7 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->n_levels = c->stage >= 2 ? c->levels : 0;
   info->log2_brick = c->logb;
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
-                          &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->bins, &c->duals,
+                          &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->duals,
                           &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);

@@ -294,84 +294,246 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
   if (lane == 0 && err) atomicOr(&sc->err, err);
 }
 
-// Partitioned form of pass 2, for large inputs: the random slot writes of
-// k_scatter_cells leave L2 as partial sectors (a read-modify-write each in
-// DRAM). Instead, k_bin_cells bins the cells by slot range (2^kBinShift slots,
-// 32 MB of records, per bin) into a staging array, writing each CTA tile's
-// cells of one bin as one contiguous run; k_place_cells then streams the
-// staging array in order, so its random record writes fall into one or two
-// bins' windows at a time and are merged in L2.
-constexpr int kBinShift = 22;
-constexpr int kMaxBins = 1 << (31 - kBinShift);   // slot indices stay below 2^31
-constexpr int kBinThreads = 256;
-constexpr int kBinPerThread = 16;
+// Binned form of pass 2. Random 8-byte stores run at one memory transaction
+// each however small the address range they fall in, so k_scatter_cells is
+// bound by its store transactions, not by DRAM. The binned form writes only
+// whole runs: a two-level radix split of the cells by slot, then one CTA per
+// window of 2^kWinShift slots builds the window's records in shared memory
+// and writes them out in full lines (empty slots included, so `rec` needs
+// no clearing).
+//   k_bin_coarse: per tile of cells, find the slot, sort the tile by coarse
+//     bin (2^kCoarseShift slots) in shared memory, append each bin's run to
+//     the bin's region of stage A (one global atomic per bin and tile);
+//   k_bin_fine: per tile of one coarse bin, the same split by window into
+//     stage B;
+//   k_place_windows: per window, scatter its entries into shared memory.
+// Stages are three 32-bit arrays each (slot, cell index, scalar bits); a
+// coarse bin holds at most 2^kCoarseShift entries and a window 2^kWinShift,
+// more means two cells in one slot (ERR_DUPLICATE).
+constexpr int kCoarseShift = 21;
+constexpr int kMaxCoarse = 1 << (31 - kCoarseShift);   // slot indices stay below 2^31
+constexpr int kWinShift = 13;
+constexpr int kWinSlots = 1 << kWinShift;
+constexpr int kFinePerCoarse = 1 << (kCoarseShift - kWinShift);
+constexpr int kBinThreads = 512;
+constexpr int kBinPerThread = 8;
 constexpr int kBinTile = kBinThreads * kBinPerThread;
+constexpr int kPlaceThreads = 512;
+
+struct Stage {
+  unsigned* slot;
+  unsigned* idx;
+  unsigned* val;
+};
+
+// Exclusive scan of cnt[0..m) in place (m <= 2 * blockDim.x) and, for every
+// non-empty entry, a run reserved in the global counter gcount[goff + b];
+// returns the total. All threads of the CTA must call it.
+__device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gbase, int m,
+                                                     unsigned* gcount, long long goff, unsigned* wsum) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  const int b0 = 2 * t, b1 = 2 * t + 1;
+  const unsigned c0 = b0 < m ? cnt[b0] : 0u, c1 = b1 < m ? cnt[b1] : 0u;
+  if (c0) gbase[b0] = atomicAdd(gcount + goff + b0, c0);
+  if (c1) gbase[b1] = atomicAdd(gcount + goff + b1, c1);
+  const unsigned v = c0 + c1;
+  unsigned incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned x = lane < nw ? wsum[lane] : 0u;
+    unsigned c = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, c, o);
+      if (lane >= o) c += y;
+    }
+    if (lane < nw) wsum[lane] = c - x;
+    if (lane == 31) wsum[32] = c;
+  }
+  __syncthreads();
+  const unsigned ex = wsum[w] + incl - v;
+  if (b0 < m) cnt[b0] = ex;
+  if (b1 < m) cnt[b1] = ex + c0;
+  const unsigned total = wsum[32];
+  __syncthreads();
+  return total;
+}
 
 template <int LOGB>
-__global__ void __launch_bounds__(kBinThreads) k_bin_cells(
+__global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl, const float* __restrict__ s,
-    long long n, Locator L, uint4* __restrict__ staging, unsigned long long* __restrict__ bin_count,
-    int n_bins, Scratch* sc) {
-  __shared__ unsigned hist[kMaxBins];
-  __shared__ unsigned long long base[kMaxBins];
-  const int t = threadIdx.x;
+    long long n, Locator L, int n_coarse, Stage A, unsigned* __restrict__ coarse_count, Scratch* sc) {
+  extern __shared__ unsigned smem[];
+  unsigned* start = smem;                     // [kMaxCoarse] counts, then run starts in the tile
+  unsigned* gbase = start + kMaxCoarse;       // [kMaxCoarse] run starts in the bins
+  unsigned* t_slot = gbase + kMaxCoarse;      // [kBinTile] the tile sorted by bin
+  unsigned* t_idx = t_slot + kBinTile;
+  unsigned* t_val = t_idx + kBinTile;
+  __shared__ unsigned wsum[33];
+  const int t = threadIdx.x, lane = t & 31;
   unsigned err = 0;
   for (long long tile0 = (long long)blockIdx.x * kBinTile; tile0 < n; tile0 += (long long)gridDim.x * kBinTile) {
-    for (int b = t; b < n_bins; b += kBinThreads) hist[b] = 0;
+    for (int b = t; b < n_coarse; b += kBinThreads) start[b] = 0;
     __syncthreads();
-    unsigned slot[kBinPerThread], rank[kBinPerThread];
+    unsigned slot[kBinPerThread], rank[kBinPerThread], val[kBinPerThread];
 #pragma unroll
-    for (int j = 0; j < kBinPerThread; ++j) {
-      const long long i = tile0 + j * kBinThreads + t;
-      slot[j] = kReject;
-      rank[j] = 0;
-      if (i >= n) continue;
-      const int x = __ldcs(xyz + 3 * i), y = __ldcs(xyz + 3 * i + 1), z = __ldcs(xyz + 3 * i + 2);
-      const int l = __ldcs(lvl + i);
-      if (!isfinite(__ldg(s + i))) err |= ERR_NONFINITE;
-      if (l > kMaxLevel) continue;
-      const int bi = find_brick(L, brick_key<LOGB>(x, y, z, l));
-      if (bi < 0) {
-        err |= ERR_HASH_FULL;
-        continue;
+    for (int h = 0; h < kBinPerThread; h += 4) {   // four cells at a time, first probes issued together
+      int loc[4];
+      unsigned long long key[4], k0[4];
+      int b0[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long i = tile0 + (long long)(h + u) * kBinThreads + t;
+        key[u] = kEmptyKey;
+        loc[u] = 0;
+        val[h + u] = 0u;
+        if (i < n) {
+          const int x = __ldcs(xyz + 3 * i), y = __ldcs(xyz + 3 * i + 1), z = __ldcs(xyz + 3 * i + 2);
+          const int l = __ldcs(lvl + i);
+          const float v = __ldcs(s + i);
+          if (!isfinite(v)) err |= ERR_NONFINITE;
+          val[h + u] = __float_as_uint(v);
+          if (l <= kMaxLevel) {
+            key[u] = brick_key<LOGB>(x, y, z, l);
+            loc[u] = (int)local_index<LOGB>(x, y, z, l);
+          }
+        }
+        const unsigned long long hh = mix64(key[u]) & L.hmask;
+        k0[u] = key[u] != kEmptyKey ? __ldg(L.hkeys + hh) : kEmptyKey;
+        b0[u] = key[u] != kEmptyKey ? __ldg(L.hvals + hh) : -1;
       }
-      slot[j] = ((unsigned)bi << (3 * LOGB)) | local_index<LOGB>(x, y, z, l);
-      rank[j] = atomicAdd(&hist[slot[j] >> kBinShift], 1u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        slot[h + u] = kReject;
+        rank[h + u] = 0;
+        if (key[u] == kEmptyKey) continue;
+        const int bi = k0[u] == key[u] ? b0[u] : find_brick(L, key[u]);
+        if (bi < 0) {
+          err |= ERR_HASH_FULL;
+          continue;
+        }
+        slot[h + u] = ((unsigned)bi << (3 * LOGB)) | (unsigned)loc[u];
+        rank[h + u] = atomicAdd(&start[slot[h + u] >> kCoarseShift], 1u);
+      }
     }
     __syncthreads();
-    for (int b = t; b < n_bins; b += kBinThreads)
-      if (hist[b]) base[b] = atomicAdd(bin_count + b, (unsigned long long)hist[b]);
-    __syncthreads();
+    const unsigned total = scan_and_reserve(start, gbase, n_coarse, coarse_count, 0, wsum);
 #pragma unroll
     for (int j = 0; j < kBinPerThread; ++j) {
       if (slot[j] == kReject) continue;
-      const long long i = tile0 + j * kBinThreads + t;
-      const unsigned b = slot[j] >> kBinShift;
-      const unsigned long long r = base[b] + rank[j];
-      if (r >= (1ull << kBinShift)) {   // more cells than slots in the bin: duplicates
+      const unsigned pos = start[slot[j] >> kCoarseShift] + rank[j];
+      t_slot[pos] = slot[j];
+      t_idx[pos] = (unsigned)(tile0 + (long long)j * kBinThreads + t);
+      t_val[pos] = val[j];
+    }
+    __syncthreads();
+    for (unsigned p = t; p < total; p += kBinThreads) {   // runs of one bin are contiguous: coalesced
+      const unsigned sl = t_slot[p];
+      const unsigned b = sl >> kCoarseShift;
+      const unsigned r = gbase[b] + (p - start[b]);
+      if (r >= (1u << kCoarseShift)) {
         err |= ERR_DUPLICATE;
         continue;
       }
-      staging[((long long)b << kBinShift) + (long long)r] =
-          make_uint4(slot[j], (unsigned)i, __float_as_uint(__ldg(s + i)), 0u);
+      const long long dst = ((long long)b << kCoarseShift) + r;
+      A.slot[dst] = sl;
+      A.idx[dst] = t_idx[p];
+      A.val[dst] = t_val[p];
     }
     __syncthreads();
+  }
+  err = warp_or(err);
+  if (lane == 0 && err) atomicOr(&sc->err, err);
+}
+
+// Grid (tiles of one coarse bin, coarse bins).
+__global__ void __launch_bounds__(kBinThreads) k_bin_fine(Stage A, const unsigned* __restrict__ coarse_count,
+                                                          Stage B, unsigned* __restrict__ win_count, Scratch* sc) {
+  extern __shared__ unsigned smem[];
+  unsigned* start = smem;                      // [kFinePerCoarse]
+  unsigned* gbase = start + kFinePerCoarse;    // [kFinePerCoarse]
+  unsigned* t_slot = gbase + kFinePerCoarse;   // [kBinTile]
+  unsigned* t_idx = t_slot + kBinTile;
+  unsigned* t_val = t_idx + kBinTile;
+  __shared__ unsigned wsum[33];
+  const int t = threadIdx.x;
+  const long long cb = blockIdx.y;
+  const unsigned cnt = min(__ldg(coarse_count + cb), 1u << kCoarseShift);
+  const unsigned tile0 = blockIdx.x * (unsigned)kBinTile;
+  if (tile0 >= cnt) return;   // uniform over the CTA
+  for (int b = t; b < kFinePerCoarse; b += kBinThreads) start[b] = 0;
+  __syncthreads();
+  unsigned slot[kBinPerThread], rank[kBinPerThread], idx[kBinPerThread], val[kBinPerThread];
+  const long long src0 = (cb << kCoarseShift) + tile0;
+#pragma unroll
+  for (int j = 0; j < kBinPerThread; ++j) {
+    const unsigned e = tile0 + j * kBinThreads + t;
+    slot[j] = kReject;
+    rank[j] = 0;
+    if (e < cnt) {
+      const long long src = src0 + j * kBinThreads + t;
+      slot[j] = __ldcs(A.slot + src);
+      idx[j] = __ldcs(A.idx + src);
+      val[j] = __ldcs(A.val + src);
+      rank[j] = atomicAdd(&start[(slot[j] >> kWinShift) & (kFinePerCoarse - 1)], 1u);
+    }
+  }
+  __syncthreads();
+  const unsigned total = scan_and_reserve(start, gbase, kFinePerCoarse, win_count, cb << (kCoarseShift - kWinShift),
+                                          wsum);
+#pragma unroll
+  for (int j = 0; j < kBinPerThread; ++j) {
+    if (slot[j] == kReject) continue;
+    const unsigned pos = start[(slot[j] >> kWinShift) & (kFinePerCoarse - 1)] + rank[j];
+    t_slot[pos] = slot[j];
+    t_idx[pos] = idx[j];
+    t_val[pos] = val[j];
+  }
+  __syncthreads();
+  unsigned err = 0;
+  for (unsigned p = t; p < total; p += kBinThreads) {
+    const unsigned sl = t_slot[p];
+    const unsigned f = (sl >> kWinShift) & (kFinePerCoarse - 1);
+    const unsigned r = gbase[f] + (p - start[f]);
+    if (r >= (unsigned)kWinSlots) {
+      err |= ERR_DUPLICATE;
+      continue;
+    }
+    const long long dst = ((long long)(sl >> kWinShift) << kWinShift) + r;
+    B.slot[dst] = sl;
+    B.idx[dst] = t_idx[p];
+    B.val[dst] = t_val[p];
   }
   err = warp_or(err);
   if ((t & 31) == 0 && err) atomicOr(&sc->err, err);
 }
 
-__global__ void __launch_bounds__(256) k_place_cells(const uint4* __restrict__ staging,
-                                                     const unsigned long long* __restrict__ bin_count,
-                                                     long long n_slots, unsigned long long* __restrict__ rec) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x; pos < n_slots; pos += stride) {
-    const long long b = pos >> kBinShift;
-    const unsigned long long cnt = min(__ldg(bin_count + b), 1ull << kBinShift);   // written entries
-    if ((unsigned long long)(pos & ((1ll << kBinShift) - 1)) >= cnt) continue;
-    const uint4 e = __ldg(staging + pos);
-    rec[e.x] = ((unsigned long long)e.z << 32) | e.y;
+// One CTA per window of kWinSlots slots.
+__global__ void __launch_bounds__(kPlaceThreads) k_place_windows(Stage B, const unsigned* __restrict__ win_count,
+                                                                 long long n_slots, unsigned long long* rec) {
+  extern __shared__ __align__(16) unsigned long long win[];   // [kWinSlots]
+  const int t = threadIdx.x;
+  const long long w0 = (long long)blockIdx.x << kWinShift;
+  for (int k = t; k < kWinSlots; k += kPlaceThreads) win[k] = kEmptyRec;
+  __syncthreads();
+  const unsigned cnt = min(__ldg(win_count + blockIdx.x), (unsigned)kWinSlots);
+  for (unsigned e = t; e < cnt; e += kPlaceThreads) {
+    const unsigned sl = __ldcs(B.slot + w0 + e);
+    win[sl & (kWinSlots - 1)] =
+        ((unsigned long long)__ldcs(B.val + w0 + e) << 32) | __ldcs(B.idx + w0 + e);
   }
+  __syncthreads();
+  // n_slots is a multiple of the brick size (>= 64), so windows end on pairs
+  const long long m = min((long long)kWinSlots, n_slots - w0);
+  ulonglong2* dst = reinterpret_cast<ulonglong2*>(rec + w0);
+  const ulonglong2* srcw = reinterpret_cast<const ulonglong2*>(win);
+  for (long long k = t; k < m / 2; k += kPlaceThreads) dst[k] = srcw[k];
 }
 
 // Pass over the slots: resolve every logical cell of every brick to the
@@ -1080,31 +1242,86 @@ cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
-                             Locator loc, long long n_slots, uint4* staging, unsigned long long* bin_count,
-                             unsigned long long* rec, Scratch* sc, int sm_count, cudaStream_t st) {
-  const int n_bins = (int)((n_slots + (1ll << kBinShift) - 1) >> kBinShift);
-  if (n <= 0 || n_bins <= 0) return cudaSuccess;
-  if (n_bins > kMaxBins) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(unsigned long long) * n_bins, st);
-  if (e != cudaSuccess) return e;
-  const long long tiles = (n + kBinTile - 1) / kBinTile;
-  const int grid = (int)(tiles < (long long)sm_count * 8 ? tiles : (long long)sm_count * 8);
-  AMR_DISPATCH(logb, (k_bin_cells<LB><<<grid, kBinThreads, 0, st>>>(xyz, lvl, s, n, loc, staging, bin_count,
-                                                                     n_bins, sc)));
-  return cudaGetLastError();
+BinLayout bin_layout(long long n_slots) {
+  BinLayout b;
+  b.n_coarse = (n_slots + (1ll << kCoarseShift) - 1) >> kCoarseShift;
+  b.n_win = (n_slots + kWinSlots - 1) >> kWinShift;
+  b.stage_a = b.n_coarse << kCoarseShift;
+  b.stage_b = b.n_win << kWinShift;
+  b.bytes = (size_t)(12 * (b.stage_a + b.stage_b) + 4 * (b.n_coarse + b.n_win));
+  return b;
 }
 
-cudaError_t launch_place(long long n_slots, const uint4* staging, const unsigned long long* bin_count,
-                         unsigned long long* rec, int sm_count, cudaStream_t st) {
+namespace {
+constexpr int kSmemCoarse = (2 * kMaxCoarse + 3 * kBinTile) * 4;
+constexpr int kSmemFine = (2 * kFinePerCoarse + 3 * kBinTile) * 4;
+constexpr int kSmemPlace = kWinSlots * 8;
+
+struct Stages {
+  Stage a, b;
+  unsigned* coarse_count;
+  unsigned* win_count;
+};
+
+Stages stages_of(const BinLayout& lay, void* staging) {
+  unsigned* base = static_cast<unsigned*>(staging);
+  unsigned* bb = base + 3 * lay.stage_a;
+  Stages S;
+  S.a = Stage{base, base + lay.stage_a, base + 2 * lay.stage_a};
+  S.b = Stage{bb, bb + lay.stage_b, bb + 2 * lay.stage_b};
+  S.coarse_count = bb + 3 * lay.stage_b;
+  S.win_count = S.coarse_count + lay.n_coarse;
+  return S;
+}
+}  // namespace
+
+cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
+                              Locator loc, long long n_slots, void* staging, Scratch* sc, int sm_count,
+                              cudaStream_t st) {
+  const BinLayout lay = bin_layout(n_slots);
   if (n_slots <= 0) return cudaSuccess;
-  k_place_cells<<<sm_count * 8, 256, 0, st>>>(staging, bin_count, n_slots, rec);
+  if (lay.n_coarse > kMaxCoarse || n > 0xFFFFFFFFll) return cudaErrorInvalidValue;
+  const Stages S = stages_of(lay, staging);
+  cudaError_t e = cudaMemsetAsync(S.coarse_count, 0, 4 * (size_t)(lay.n_coarse + lay.n_win), st);
+  if (e != cudaSuccess) return e;
+  static bool attrs = false;   // dynamic shared memory above the 48 KB default: opt in once
+  if (!attrs) {
+    if ((e = cudaFuncSetAttribute(k_bin_coarse<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
+        (e = cudaFuncSetAttribute(k_bin_coarse<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
+        (e = cudaFuncSetAttribute(k_bin_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFine)) ||
+        (e = cudaFuncSetAttribute(k_place_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)))
+      return e;
+    attrs = true;
+  }
+  if (n <= 0) return cudaSuccess;
+  const long long tiles = (n + kBinTile - 1) / kBinTile;
+  AMR_DISPATCH(logb, ({
+    int per_sm = 0;   // one resident wave: the tile loop is grid-strided
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_coarse<LB>, kBinThreads,
+                                                           kSmemCoarse)) != cudaSuccess)
+      return e;
+    const int grid = (int)std::min<long long>(tiles, (long long)sm_count * std::max(per_sm, 1));
+    k_bin_coarse<LB><<<grid, kBinThreads, kSmemCoarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse, S.a,
+                                                             S.coarse_count, sc);
+  }));
   return cudaGetLastError();
 }
 
-size_t bin_staging_bytes(long long n_slots) {
-  const long long n_bins = (n_slots + (1ll << kBinShift) - 1) >> kBinShift;
-  return (size_t)(n_bins << kBinShift) * sizeof(uint4);
+cudaError_t launch_bin_fine(long long n_slots, void* staging, Scratch* sc, cudaStream_t st) {
+  const BinLayout lay = bin_layout(n_slots);
+  if (n_slots <= 0) return cudaSuccess;
+  const Stages S = stages_of(lay, staging);
+  k_bin_fine<<<dim3((1u << kCoarseShift) / kBinTile, (unsigned)lay.n_coarse), kBinThreads, kSmemFine, st>>>(
+      S.a, S.coarse_count, S.b, S.win_count, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_place_windows(long long n_slots, void* staging, unsigned long long* rec, cudaStream_t st) {
+  const BinLayout lay = bin_layout(n_slots);
+  if (n_slots <= 0) return cudaSuccess;
+  const Stages S = stages_of(lay, staging);
+  k_place_windows<<<(unsigned)lay.n_win, kPlaceThreads, kSmemPlace, st>>>(S.b, S.win_count, n_slots, rec);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, float* scal, long long n_slots,

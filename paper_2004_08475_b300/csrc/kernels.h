@@ -73,14 +73,21 @@ cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* 
                                  long long n, Locator loc, unsigned long long* rec, Scratch* sc,
                                  int grid, int block, cudaStream_t st);
 
-// Partitioned scatter for large inputs (same result as launch_scatter_cells):
-// staging must hold bin_staging_bytes(n_slots) bytes, bin_count 512 counters.
-cudaError_t launch_bin(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
-                       Locator loc, long long n_slots, uint4* staging, unsigned long long* bin_count,
-                       unsigned long long* rec, Scratch* sc, int sm_count, cudaStream_t st);
-cudaError_t launch_place(long long n_slots, const uint4* staging, const unsigned long long* bin_count,
-                         unsigned long long* rec, int sm_count, cudaStream_t st);
-size_t bin_staging_bytes(long long n_slots);
+// Binned cell placement, same result as launch_scatter_cells (three passes;
+// see kernels.cu). All three take the
+// same staging buffer of bin_layout(n_slots).bytes bytes; launch_bin_coarse
+// clears its counters first. Together they write every slot of rec (empty
+// slots as kEmptyRec).
+struct BinLayout {
+  long long n_coarse = 0, n_win = 0, stage_a = 0, stage_b = 0;
+  size_t bytes = 0;
+};
+BinLayout bin_layout(long long n_slots);
+cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
+                              Locator loc, long long n_slots, void* staging, Scratch* sc, int sm_count,
+                              cudaStream_t st);
+cudaError_t launch_bin_fine(long long n_slots, void* staging, Scratch* sc, cudaStream_t st);
+cudaError_t launch_place_windows(long long n_slots, void* staging, unsigned long long* rec, cudaStream_t st);
 
 // Writes view[] and scal[] of every slot from rec[].
 cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, float* scal, long long n_slots,

@@ -247,6 +247,7 @@ class Server:
                 ctx.upload(ds.xyz, ds.lvl, ds.s)
                 ctx.build_locator(**ds.opts)
                 ctx.dual_cells()
+                ctx.trim()   # resident data sets keep no placement workspace
             except Exception:
                 ctx.close()
                 raise

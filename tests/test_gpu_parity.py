@@ -87,6 +87,40 @@ def test_partitioned_duplicate_detected():
     assert e.value.code == amriso.ERR_DUPLICATE
 
 
+def test_trim_keeps_results():
+    """amr_trim frees the placement workspace; the resident locator and dual
+    cells still give the same triangles."""
+    from paper_2004_08475_b300 import amriso
+    xyz, lv, s, iso, info = synth.octree_gaussians(seed=5, roots=8, root_level=5)
+    ctx = amriso.AmrContext()
+    ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+    ctx.build_locator(partitioned=1)
+    ctx.dual_cells()
+    before = ctx.info().device_bytes
+    a = canonical(ctx.iso(iso).cpu().numpy())
+    ctx.trim()
+    after = ctx.info().device_bytes
+    assert after < before
+    b = canonical(ctx.iso(iso, host=True).numpy())   # host delivery re-creates its staging
+    assert a.shape[0] > 0 and np.array_equal(a.view(np.int32), b.view(np.int32))
+
+
+@pytest.mark.parametrize("copies", [3, 9000])
+def test_binned_window_overflow_is_duplicate(copies):
+    """More copies of one cell than a window of the binned placement holds
+    are caught by the capacity check, not written past the window."""
+    from paper_2004_08475_b300 import amriso
+    xyz = torch.zeros((copies + 1, 3), dtype=torch.int32)
+    xyz[0, 0] = 8
+    lv = torch.zeros(copies + 1, dtype=torch.uint8)
+    s = torch.arange(copies + 1, dtype=torch.float32)
+    ctx = amriso.AmrContext()
+    ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+    with pytest.raises(amriso.AmrError) as e:
+        ctx.build_locator(partitioned=1)
+    assert e.value.code == amriso.ERR_DUPLICATE
+
+
 @pytest.mark.parametrize("seed", range(24))
 def test_random_octrees(seed):
     levels = 2 + seed % 4
