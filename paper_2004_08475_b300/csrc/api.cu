@@ -77,7 +77,7 @@ struct amr_ctx {
   float alpha = 0.5f;
   int block = 256;
   int check_overlap = 0;
-  DevBuf hkeys, hvals, bricks, rec, scal, view, nbr, staging;
+  DevBuf htab, bricks, rec, scal, view, nbr, staging;
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
   int levels = 0;
@@ -199,8 +199,7 @@ int err_code(unsigned e) {
 
 Locator make_locator(amr_ctx* c) {
   Locator L;
-  L.hkeys = static_cast<const unsigned long long*>(c->hkeys.p);
-  L.hvals = static_cast<const int*>(c->hvals.p);
+  L.htab = static_cast<const ulonglong2*>(c->htab.p);
   L.hmask = c->hcap - 1;
   L.bricks = static_cast<const int4*>(c->bricks.p);
   L.rec = static_cast<const unsigned long long*>(c->rec.p);
@@ -290,7 +289,7 @@ void amr_destroy(amr_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
+  DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
                     &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->duals, &c->scratch,
                     &c->stage_buf, &c->iso_buf, &c->seg_buf};
   for (DevBuf* b : bufs) release(*b);
@@ -380,7 +379,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   const long long n = c->n;
   const int B3 = 1 << (3 * logb);
   // Table size: bricks expected at least 1/4 full, but start no larger than
-  // 2^22 entries (48 MB) so the table stays in L2 while every cell probes
+  // 2^22 entries (64 MB) so the table stays in L2 while every cell probes
   // it. A table that fills up stops the insert early and is rebuilt larger.
   unsigned long long want = (unsigned long long)((double)(n * 4 / B3 + 64) / alpha);
   want = std::min<unsigned long long>(want, 1ull << 22);
@@ -388,16 +387,14 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
     c->hcap = pow2_at_least(want);
     const unsigned long long limit =
         (unsigned long long)((double)c->hcap * std::min(0.85, 2.0 * (double)alpha));
-    AMR_TRY(ensure(c->hkeys, c->hcap * 8));
-    AMR_TRY(ensure(c->hvals, c->hcap * 4));
+    AMR_TRY(ensure(c->htab, c->hcap * 16));
     AMR_TRY(ensure(c->bricks, c->hcap * 16));
-    AMR_CUDA(cudaMemsetAsync(c->hkeys.p, 0xFF, c->hcap * 8, c->stream));
+    AMR_CUDA(cudaMemsetAsync(c->htab.p, 0xFF, c->hcap * 16, c->stream));
     AMR_TRY(reset_scratch(c));
     if (n > 0) {
       KernelTimer kt(c, KT_INSERT);
       AMR_CUDA(launch_insert_bricks(logb, c->xyz, c->lvl, c->s, n,
-                                    static_cast<unsigned long long*>(c->hkeys.p),
-                                    static_cast<int*>(c->hvals.p), c->hcap - 1,
+                                    static_cast<ulonglong2*>(c->htab.p), c->hcap - 1,
                                     static_cast<int4*>(c->bricks.p), limit, dev_sc(c),
                                     grid_for(c, n, block, 2048 / block), block, c->stream));
     }
@@ -705,7 +702,7 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->n_dual = c->stage >= 3 ? c->n_dual : -1;
   info->n_levels = c->stage >= 2 ? c->levels : 0;
   info->log2_brick = c->logb;
-  const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->hkeys, &c->hvals, &c->bricks,
+  const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
                           &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->duals,
                           &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf};
   long long total = 0;

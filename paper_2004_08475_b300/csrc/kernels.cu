@@ -2,7 +2,7 @@
 //
 // Data layout in HBM (one data set):
 //   input        xyz[n][3] int32, level[n] u8, scalar[n] f32 (caller order)
-//   brick hash   hkeys[hcap] u64 key = (level, brick coords) -> hvals[hcap] brick index
+//   brick hash   htab[hcap] 16-byte entries {u64 key = (level, brick coords), brick index}
 //   bricks       bricks[n_bricks] int4 = lower corner of the brick (finest
 //                units) and its level; a level-l brick covers B^3 logical
 //                level-l cells, B = 2^LOGB
@@ -78,9 +78,9 @@ __device__ __forceinline__ unsigned local_index(int x, int y, int z, int l) {
 __device__ __forceinline__ int find_brick(const Locator& L, unsigned long long key) {
   unsigned long long h = mix64(key) & L.hmask;
   for (unsigned long long p = 0; p <= L.hmask; ++p) {
-    const unsigned long long k = __ldg(L.hkeys + h);
-    if (k == key) return __ldg(L.hvals + h);
-    if (k == kEmptyKey) return -1;
+    const ulonglong2 e = __ldg(L.htab + h);
+    if (e.x == key) return (int)e.y;
+    if (e.x == kEmptyKey) return -1;
     h = (h + 1) & L.hmask;
   }
   return -1;
@@ -113,7 +113,7 @@ constexpr int kUnroll = 4;   // cells per lane per trip of the cell-parallel loo
 template <int LOGB>
 __global__ void __launch_bounds__(1024) k_insert_bricks(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
-    const float* __restrict__ s, long long n, unsigned long long* hkeys, int* hvals,
+    const float* __restrict__ s, long long n, ulonglong2* htab,
     unsigned long long hmask, int4* bricks, unsigned long long brick_limit, Scratch* sc) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
       }
       lead[u] = key[u] != kEmptyKey;
       h[u] = mix64(key[u]) & hmask;
-      cur[u] = lead[u] ? __ldcg(hkeys + h[u]) : 0ull;   // independent first probes
+      cur[u] = lead[u] ? __ldcg(&htab[h[u]].x) : 0ull;   // independent first probes
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -172,16 +172,19 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
       unsigned long long hh = h[u];
       bool done = false;
       for (unsigned long long p = 0; p < limit; ++p) {
-        const unsigned long long c = p == 0 ? cur[u] : __ldcg(hkeys + hh);
+        const unsigned long long c = p == 0 ? cur[u] : __ldcg(&htab[hh].x);
         if (c == key[u]) { done = true; break; }
         if (c == kEmptyKey) {
-          const unsigned long long prev = atomicCAS(hkeys + hh, kEmptyKey, key[u]);
+          const unsigned long long prev = atomicCAS(&htab[hh].x, kEmptyKey, key[u]);
           if (prev == kEmptyKey) {
             const unsigned long long bi = atomicAdd(&sc->n_bricks, 1ull);
-            if (bi >= brick_limit) atomicOr(&sc->err, (unsigned)ERR_HASH_FULL);
-            hvals[hh] = (int)bi;
-            const int m = ~((1 << (l[u] + LOGB)) - 1);
-            bricks[bi] = make_int4(x[u] & m, y[u] & m, z[u] & m, l[u]);
+            htab[hh].y = bi;
+            if (bi < brick_limit) {   // bricks[] holds brick_limit entries
+              const int m = ~((1 << (l[u] + LOGB)) - 1);
+              bricks[bi] = make_int4(x[u] & m, y[u] & m, z[u] & m, l[u]);
+            } else {
+              atomicOr(&sc->err, (unsigned)ERR_HASH_FULL);
+            }
             done = true;
             break;
           }
@@ -274,8 +277,9 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
     for (int u = 0; u < kUnroll; ++u) {   // first probe of every key, issued together
       key[u] = (l[u] >= 0 && l[u] <= kMaxLevel) ? brick_key<LOGB>(x[u], y[u], z[u], l[u]) : kEmptyKey;
       const unsigned long long h = mix64(key[u]) & L.hmask;
-      k0[u] = key[u] != kEmptyKey ? __ldg(L.hkeys + h) : kEmptyKey;
-      b0[u] = key[u] != kEmptyKey ? __ldg(L.hvals + h) : -1;
+      const ulonglong2 e = key[u] != kEmptyKey ? __ldg(L.htab + h) : make_ulonglong2(kEmptyKey, ~0ull);
+      k0[u] = e.x;
+      b0[u] = (int)e.y;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -405,8 +409,9 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
           }
         }
         const unsigned long long hh = mix64(key[u]) & L.hmask;
-        k0[u] = key[u] != kEmptyKey ? __ldg(L.hkeys + hh) : kEmptyKey;
-        b0[u] = key[u] != kEmptyKey ? __ldg(L.hvals + hh) : -1;
+        const ulonglong2 e = key[u] != kEmptyKey ? __ldg(L.htab + hh) : make_ulonglong2(kEmptyKey, ~0ull);
+        k0[u] = e.x;
+        b0[u] = (int)e.y;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -647,6 +652,48 @@ __host__ __device__ constexpr DualMasks make_dual_masks() {
 
 __constant__ DualMasks c_masks = make_dual_masks();
 
+// The one-cell halo of a brick's (B+2)^3 region as a list, so that the
+// threads load it without walking (and skipping) the interior: per entry
+// the region coordinates rx, ry, rz (4 bits each), the neighbour region
+// nbi = 0..26 (5 bits) and the Morton index of the cell inside a same-level
+// neighbour brick (from bit 17).
+template <int LOGB>
+struct HaloList {
+  static constexpr int B = 1 << LOGB, R = B + 2;
+  static constexpr int kCount = R * R * R - B * B * B;
+  unsigned e[kCount];
+};
+
+template <int LOGB>
+__host__ __device__ constexpr HaloList<LOGB> make_halo_list() {
+  HaloList<LOGB> h{};
+  constexpr int B = HaloList<LOGB>::B, R = HaloList<LOGB>::R;
+  int k = 0;
+  for (int rz = 0; rz < R; ++rz)
+    for (int ry = 0; ry < R; ++ry)
+      for (int rx = 0; rx < R; ++rx) {
+        if (rx >= 1 && rx <= B && ry >= 1 && ry <= B && rz >= 1 && rz <= B) continue;
+        const int nbi = (rx == 0 ? 0 : (rx == R - 1 ? 2 : 1)) + 3 * (ry == 0 ? 0 : (ry == R - 1 ? 2 : 1)) +
+                        9 * (rz == 0 ? 0 : (rz == R - 1 ? 2 : 1));
+        const int lx = (rx - 1 + B) % B, ly = (ry - 1 + B) % B, lz = (rz - 1 + B) % B;
+        unsigned m = 0;
+        for (int b = 0; b < LOGB; ++b)
+          m |= (unsigned)(((lx >> b) & 1) << (3 * b)) | (unsigned)(((ly >> b) & 1) << (3 * b + 1)) |
+               (unsigned)(((lz >> b) & 1) << (3 * b + 2));
+        h.e[k++] = (unsigned)rx | ((unsigned)ry << 4) | ((unsigned)rz << 8) | ((unsigned)nbi << 12) | (m << 17);
+      }
+  return h;
+}
+
+__device__ const HaloList<2> g_halo2 = make_halo_list<2>();
+__device__ const HaloList<3> g_halo3 = make_halo_list<3>();
+
+template <int LOGB>
+__device__ __forceinline__ const unsigned* halo_list() {
+  if constexpr (LOGB == 2) return g_halo2.e;
+  else return g_halo3.e;
+}
+
 // ---------------------------------------------------------------------------
 // Marching Cubes on dual cells (Sec. 5, 5.1, 5.2)
 // ---------------------------------------------------------------------------
@@ -830,7 +877,6 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
   constexpr unsigned kSame = 0x80000000u;   // slot indices stay below 2^31
   __shared__ unsigned rv[NR];
   __shared__ unsigned rmask[R * R];
-  __shared__ int nb[27];
   __shared__ unsigned wsum[NW + 1];
   __shared__ unsigned long long cta_base;
   __shared__ float rsc[ISO ? NR : 1];                 // scalars of the region's cells
@@ -851,52 +897,53 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     pz[j] = compact<LOGB>(m >> 2);
     c0[j] = px[j] + R * (py[j] + R * pz[j]);   // neighbourhood origin (cell - 1)
   }
+  for (int row = t; row < R * R; row += NT) rmask[row] = 0;   // cleared again after each use
+  __syncthreads();
   for (long long bi = blockIdx.x; bi < n_bricks; bi += gridDim.x) {
     const int4 b = __ldg(L.bricks + bi);
     const int l = b.w;
-    if (t < 27) nb[t] = __ldg(nbr + bi * 27 + t);
     bool mine[CPT];
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {   // the brick itself: coalesced reads
       const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)(t + j * NT);
       const unsigned v = __ldg(L.view + s2);
       mine[j] = v == s2;
-      rv[c0[j] + 1 + R + R * R] = mine[j] ? (v | kSame) : v;
+      const int r = c0[j] + 1 + R + R * R;
+      rv[r] = mine[j] ? (v | kSame) : v;
+      if (v != kReject)
+        atomicOr(&rmask[(py[j] + 1) + R * (pz[j] + 1)],
+                 (1u << (px[j] + 1)) | ((mine[j] ? 1u : 0u) << (16 + px[j] + 1)));
     }
-    __syncthreads();
-    for (int r = t; r < NR; r += NT) {   // the one-cell halo
-      const int rx = r % R, ry = (r / R) % R, rz = r / (R * R);
-      if (rx >= 1 && rx <= B && ry >= 1 && ry <= B && rz >= 1 && rz <= B) continue;
-      const int nbi = (rx == 0 ? 0 : (rx == R - 1 ? 2 : 1)) + 3 * (ry == 0 ? 0 : (ry == R - 1 ? 2 : 1)) +
-                      9 * (rz == 0 ? 0 : (rz == R - 1 ? 2 : 1));
-      const int e = nb[nbi];
+    const unsigned* halo = halo_list<LOGB>();
+    for (int k = t; k < HaloList<LOGB>::kCount; k += NT) {   // the one-cell halo
+      const unsigned h = __ldg(halo + k);
+      const int rx = (int)(h & 15u), ry = (int)((h >> 4) & 15u), rz = (int)((h >> 8) & 15u);
+      const int e = __ldg(nbr + bi * 27 + ((h >> 12) & 31u));
       unsigned v = kReject;
+      bool same = false;
       if (e >= 0) {
         const int fb = e & ((1 << 27) - 1), lv = e >> 27;
-        const int x = b.x + ((rx - 1) << l), y = b.y + ((ry - 1) << l), z = b.z + ((rz - 1) << l);
-        const unsigned s2 = ((unsigned)fb << (3 * LOGB)) | local_index<LOGB>(x, y, z, lv);
+        unsigned s2;
+        if (lv == l) {
+          s2 = ((unsigned)fb << (3 * LOGB)) | (h >> 17);
+        } else {
+          const int x = b.x + ((rx - 1) << l), y = b.y + ((ry - 1) << l), z = b.z + ((rz - 1) << l);
+          s2 = ((unsigned)fb << (3 * LOGB)) | local_index<LOGB>(x, y, z, lv);
+        }
         v = __ldg(L.view + s2);
-        if (lv == l && v == s2) v |= kSame;
+        same = lv == l && v == s2;
       }
-      rv[r] = v;
+      rv[rx + R * (ry + R * rz)] = same ? (v | kSame) : v;
+      if (v != kReject) atomicOr(&rmask[ry + R * rz], (1u << rx) | ((same ? 1u : 0u) << (16 + rx)));
     }
     __syncthreads();
-    for (int row = t; row < R * R; row += NT) {
-      unsigned m = 0;
-#pragma unroll
-      for (int rx = 0; rx < R; ++rx) {
-        const unsigned v = rv[row * R + rx];
-        if (v != kReject) m |= (1u << rx) | ((v >> 31) << (16 + rx));
-      }
-      rmask[row] = m;
-    }
     if (ISO) {
       for (int r = t; r < NR; r += NT) {
         const unsigned v = rv[r];
         rsc[r] = v != kReject ? __ldg(L.scal + (v & ~kSame)) : 0.f;
       }
+      __syncthreads();
     }
-    __syncthreads();
     unsigned emit[CPT];
     unsigned cnt = 0;   // per-thread dual count of cell j in bits 16j..16j+15
 #pragma unroll
@@ -931,6 +978,7 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     }
     if (lane == 31) wsum[wp] = incl;
     __syncthreads();
+    for (int row = t; row < R * R; row += NT) rmask[row] = 0;   // every cell has read its masks
     if (t == 0) {
       unsigned run = 0;
       for (int w = 0; w < NW; ++w) {
@@ -1226,11 +1274,11 @@ __global__ void __launch_bounds__(256) k_get_duals(const uint4* __restrict__ dua
   } while (0)
 
 cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
-                                 long long n, unsigned long long* hkeys, int* hvals,
+                                 long long n, ulonglong2* htab,
                                  unsigned long long hmask, int4* bricks,
                                  unsigned long long brick_limit, Scratch* sc, int grid, int block,
                                  cudaStream_t st) {
-  AMR_DISPATCH(logb, (k_insert_bricks<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, hkeys, hvals, hmask,
+  AMR_DISPATCH(logb, (k_insert_bricks<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, htab, hmask,
                                                                    bricks, brick_limit, sc)));
   return cudaGetLastError();
 }

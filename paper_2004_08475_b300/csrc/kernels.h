@@ -38,8 +38,8 @@ struct Scratch {
 
 // Device view of the point-location structure (Sec. 3.2).
 struct Locator {
-  const unsigned long long* hkeys;  // [hcap] brick keys (level, brick coords)
-  const int* hvals;                 // [hcap] brick index
+  const ulonglong2* htab;           // [hcap] {brick key (level, brick coords), brick index}:
+                                    //   one 16-byte entry, so a probe is one memory transaction
   unsigned long long hmask;         // hcap - 1 (hcap a power of two)
   const int4* bricks;               // [n_bricks] origin x,y,z (finest units), level
   const unsigned long long* rec;    // [n_slots] occupant: input index (low 32 bits, all ones
@@ -61,9 +61,10 @@ struct McConst {
 // Each returns the launch's cudaError_t (cudaGetLastError after launch).
 
 // brick_limit: once this many bricks exist the table counts as full
-// (ERR_HASH_FULL is raised and the remaining inserts stop early).
+// (ERR_HASH_FULL is raised and the remaining inserts stop early); bricks[]
+// must hold brick_limit entries. htab must be all ones before the launch.
 cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
-                                 long long n, unsigned long long* hkeys, int* hvals,
+                                 long long n, ulonglong2* htab,
                                  unsigned long long hmask, int4* bricks,
                                  unsigned long long brick_limit, Scratch* sc, int grid, int block,
                                  cudaStream_t st);

@@ -35,9 +35,8 @@ constexpr long long kMaxDuals = 2 * kMaxCells;
 // Byte offsets of the pieces inside the scratch array (256-byte aligned).
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kOffScratch = 0;
-constexpr size_t kOffKeys = align256(kOffScratch + sizeof(Scratch));
-constexpr size_t kOffVals = align256(kOffKeys + kHashCap * 8);
-constexpr size_t kOffBricks = align256(kOffVals + kHashCap * 4);
+constexpr size_t kOffTable = align256(kOffScratch + sizeof(Scratch));
+constexpr size_t kOffBricks = align256(kOffTable + kHashCap * 16);
 constexpr size_t kOffRec = align256(kOffBricks + kMaxCells * 16);   // a brick holds >= 1 cell
 constexpr size_t kOffScal = align256(kOffRec + kMaxSlots * 8);
 constexpr size_t kOffView = align256(kOffScal + kMaxSlots * 4);
@@ -132,8 +131,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
   unsigned char* base = nullptr;
   NA_TRY(scratch_for_current_device(&base));
   Scratch* sc = reinterpret_cast<Scratch*>(base + kOffScratch);
-  unsigned long long* hkeys = reinterpret_cast<unsigned long long*>(base + kOffKeys);
-  int* hvals = reinterpret_cast<int*>(base + kOffVals);
+  ulonglong2* htab = reinterpret_cast<ulonglong2*>(base + kOffTable);
   int4* bricks = reinterpret_cast<int4*>(base + kOffBricks);
   unsigned long long* rec = reinterpret_cast<unsigned long long*>(base + kOffRec);
   float* scal = reinterpret_cast<float*>(base + kOffScal);
@@ -152,11 +150,11 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
     h.hi[a] = INT_MIN;
   }
   NA_TRY(rc_of(cudaMemcpyAsync(sc, &h, sizeof(Scratch), cudaMemcpyHostToDevice, st)));
-  NA_TRY(rc_of(cudaMemsetAsync(hkeys, 0xFF, kHashCap * 8, st)));
+  NA_TRY(rc_of(cudaMemsetAsync(htab, 0xFF, kHashCap * 16, st)));
   const int block = 256;
   const int grid_cells = (int)std::max(1ll, std::min((long long)(n + block - 1) / block, (long long)sms * 8));
   if (n > 0)
-    NA_TRY(rc_of(launch_insert_bricks(kLogB, xyz, level, scalar, n, hkeys, hvals, kHashCap - 1, bricks,
+    NA_TRY(rc_of(launch_insert_bricks(kLogB, xyz, level, scalar, n, htab, kHashCap - 1, bricks,
                                       kMaxCells, sc, grid_cells, block, st)));
   NA_TRY(read_counters(sc, &h, st));
   NA_TRY(err_bits(h.err));
@@ -169,8 +167,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
       return AMR_ERR_RANGE;
 
   Locator L;
-  L.hkeys = hkeys;
-  L.hvals = hvals;
+  L.htab = htab;
   L.hmask = kHashCap - 1;
   L.bricks = bricks;
   L.rec = rec;
