@@ -48,6 +48,10 @@ WORKLOADS = {
     # stand-in on which ncu captures of the wing's kernels are taken
     "wing_eighth": ("wing_bands at half the root grid per axis (profiling stand-in)",
                     lambda dev: synth.wing_bands(device=dev, dims=(224, 224, 48), scale=0.5)),
+    # 9.5M cells (80 % finest level, like the full wing's 86 %), about 1 GB
+    # on the device: the stand-in for multi-pass ncu captures
+    "wing_small": ("wing_bands at a quarter of the root grid per axis (profiling stand-in)",
+                   lambda dev: synth.wing_bands(device=dev, dims=(112, 112, 24), scale=0.25)),
 }
 
 

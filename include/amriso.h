@@ -189,6 +189,13 @@ int amr_trim(amr_ctx* ctx);
 /* Human-readable text for a return code (static storage). */
 const char* amr_strerror(int code);
 
+/* Layout version of this header's structs and signatures (AMR_ABI_VERSION
+ * of the build); a binding compares it with the header it was written for
+ * and refuses a library built from other sources. No counterpart in the
+ * paper. */
+#define AMR_ABI_VERSION 3
+int amr_abi_version(void);
+
 /* ---- introspection (host only, no device needed) ------------------------ */
 
 /* The Marching Cubes triangle table the kernels use (Sec. 5.1; generated by

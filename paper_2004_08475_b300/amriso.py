@@ -62,6 +62,9 @@ class _Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+ABI_VERSION = 3   # AMR_ABI_VERSION of include/amriso.h
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libamriso.so not built ({LIB_PATH}); run "
@@ -90,11 +93,15 @@ def _load() -> ctypes.CDLL:
         "amr_kernel_times": (I, [P, P, P, I]),
         "amr_kernel_name": (ctypes.c_char_p, [I]),
         "amr_extract_noalloc": (I, [P, P, P, I64, F, P, I64, ctypes.POINTER(I64), P]),
+        "amr_abi_version": (I, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    if lib.amr_abi_version() != ABI_VERSION:   # structs above must match the library's
+        raise ImportError(f"libamriso.so has ABI {lib.amr_abi_version()}, this binding {ABI_VERSION}: "
+                          "rebuild it (`python -m paper_2004_08475_b300.build`)")
     return lib
 
 
@@ -105,7 +112,7 @@ EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_bui
            "amr_dual_cells", "amr_get_duals", "amr_iso", "amr_iso_cases", "amr_iso_batch",
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
            "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async",
-           "amr_dual_cells_iso", "amr_trim")
+           "amr_dual_cells_iso", "amr_trim", "amr_abi_version")
 
 
 def lib() -> ctypes.CDLL:

@@ -233,6 +233,8 @@ int deliver(amr_ctx* c, void* dst, const void* src, size_t bytes, int flags) {
 
 extern "C" {
 
+int amr_abi_version(void) { return AMR_ABI_VERSION; }
+
 const char* amr_strerror(int code) {
   switch (code) {
     case AMR_OK: return "ok";

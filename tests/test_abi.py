@@ -37,6 +37,11 @@ def test_exports_every_declared_symbol(amriso):
     assert set(names) == set(amriso.EXPORTS)
 
 
+def test_abi_version_matches_header(amriso):
+    m = re.search(r"#define AMR_ABI_VERSION (\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == amriso.ABI_VERSION == amriso.lib().amr_abi_version()
+
+
 def test_strerror(amriso):
     for code in range(0, -12, -1):
         assert amriso.strerror(code)
