@@ -11,7 +11,9 @@
 //                occupant, all ones when empty), scal[] (its scalar), view[]
 //                (the slot of the actual cell containing the logical cell:
 //                itself, a coarser cell, or kReject)
-//   dual cells   duals[D] = 2 x uint4: the 8 vertex slots, order ex+2ey+4ez
+//   dual cells   duals[D] = 2 x uint4: the 8 vertex slots, order ex+2ey+4ez;
+//                bit 31 of the first is set when all 8 vertices are cells of
+//                one level at 8 different positions (hence 8 different cells)
 //   triangles    tris[T][3][3] f32
 //
 // snap() of Sec. 3.2 becomes: find the brick of the query at the query's
@@ -710,11 +712,15 @@ __device__ __forceinline__ void load_mc(McShared& sh, const McConst& mc) {
   }
 }
 
-__device__ __forceinline__ void load_dual(const uint4* __restrict__ duals, long long d, unsigned v[8]) {
+constexpr unsigned kDistinct = 0x80000000u;   // dual flag: 8 different cells (slots stay below 2^31)
+
+// Reads dual d; returns its kDistinct flag (cleared from v[0]).
+__device__ __forceinline__ bool load_dual(const uint4* __restrict__ duals, long long d, unsigned v[8]) {
   const uint4 a = __ldcs(duals + 2 * d);   // streamed: keep the scalars in L2 instead
   const uint4 c = __ldcs(duals + 2 * d + 1);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[0] = a.x & ~kDistinct; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
+  return (a.x & kDistinct) != 0;
 }
 
 // v[i] for a run-time i without moving v to local memory.
@@ -743,6 +749,13 @@ __device__ __forceinline__ unsigned kept_triangles(unsigned long long packed, in
     if (k0 != k1 && k1 != k2 && k0 != k2) keep |= 1u << t;
   }
   return keep;
+}
+
+// kept_triangles, short-cut for a dual of 8 different cells: no two of its
+// edges share an edge key, so every triangle of the case is kept.
+__device__ __forceinline__ unsigned kept_of(bool distinct, unsigned long long packed, int cnt, const unsigned v[8],
+                                            unsigned long long ea, unsigned long long eb) {
+  return distinct ? (1u << cnt) - 1u : kept_triangles(packed, cnt, v, ea, eb);
 }
 
 // Interpolated vertex on the edge between cells a and b: from the cell with
@@ -819,7 +832,31 @@ __device__ __forceinline__ void write_triangles(const int4* __restrict__ bricks,
   }
 }
 
+// Same triangles into a contiguous buffer (no capacity check): out[9 t'...]
+// for the t'-th kept triangle.
+template <int LOGB>
+__device__ __forceinline__ void stage_triangles(const int4* __restrict__ bricks, const unsigned* vr,
+                                                const float* sr, float iso, unsigned long long packed,
+                                                unsigned keep, float* out, unsigned long long ea,
+                                                unsigned long long eb) {
+  for (int t = 0; t < 5; ++t) {
+    if (!((keep >> t) & 1u)) continue;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int k = (int)((packed >> (12 * t + 4 * c)) & 15);
+      const int a = (int)((ea >> (4 * k)) & 15), b = (int)((eb >> (4 * k)) & 15);
+      const float3 q = edge_vertex(slot_cell<LOGB>(bricks, vr[a]), sr[a], slot_cell<LOGB>(bricks, vr[b]), sr[b],
+                                   iso);
+      out[3 * c + 0] = q.x;
+      out[3 * c + 1] = q.y;
+      out[3 * c + 2] = q.z;
+    }
+    out += 9;
+  }
+}
+
 constexpr int kRow = 9;   // shared-memory row stride (words): conflict-free across a warp
+constexpr int kTriStage = 80;   // triangles a warp stages in shared memory per step
 
 __device__ __forceinline__ void stage_row(unsigned* vr, float* sr, const unsigned v[8], const float sv[8]) {
 #pragma unroll
@@ -873,13 +910,19 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
   constexpr int NT = DualShape<LOGB>::kThreads;
   constexpr int CPT = DualShape<LOGB>::kPerThread;
   constexpr int NR = R * R * R;
+  // padded region layout: row stride RS, plane stride PS, chosen so that the
+  // 32 cells of a warp (a 4x4x2 Morton block) hit 32 different banks
+  constexpr int RS = R + 2;
+  constexpr int PS = ((RS * R + 15) / 32) * 32 + (RS % 8 == 0 ? 4 : 16) +
+                     (((RS * R + 15) / 32) * 32 + (RS % 8 == 0 ? 4 : 16) < RS * R ? 32 : 0);
+  constexpr int NP = PS * R;
   constexpr int NW = (NT + 31) / 32;
   constexpr unsigned kSame = 0x80000000u;   // slot indices stay below 2^31
-  __shared__ unsigned rv[NR];
+  __shared__ unsigned rv[NP];
   __shared__ unsigned rmask[R * R];
   __shared__ unsigned wsum[NW + 1];
   __shared__ unsigned long long cta_base;
-  __shared__ float rsc[ISO ? NR : 1];                 // scalars of the region's cells
+  __shared__ float rsc[ISO ? NP : 1];                 // scalars of the region's cells
   __shared__ McShared msh;
   __shared__ unsigned row_v[ISO ? NT * kRow : 1];
   __shared__ float row_s[ISO ? NT * kRow : 1];
@@ -895,7 +938,7 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     px[j] = compact<LOGB>(m);
     py[j] = compact<LOGB>(m >> 1);
     pz[j] = compact<LOGB>(m >> 2);
-    c0[j] = px[j] + R * (py[j] + R * pz[j]);   // neighbourhood origin (cell - 1)
+    c0[j] = px[j] + RS * py[j] + PS * pz[j];   // neighbourhood origin (cell - 1)
   }
   for (int row = t; row < R * R; row += NT) rmask[row] = 0;   // cleared again after each use
   __syncthreads();
@@ -908,7 +951,7 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
       const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)(t + j * NT);
       const unsigned v = __ldg(L.view + s2);
       mine[j] = v == s2;
-      const int r = c0[j] + 1 + R + R * R;
+      const int r = c0[j] + 1 + RS + PS;
       rv[r] = mine[j] ? (v | kSame) : v;
       if (v != kReject)
         atomicOr(&rmask[(py[j] + 1) + R * (pz[j] + 1)],
@@ -933,12 +976,13 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
         v = __ldg(L.view + s2);
         same = lv == l && v == s2;
       }
-      rv[rx + R * (ry + R * rz)] = same ? (v | kSame) : v;
+      rv[rx + RS * ry + PS * rz] = same ? (v | kSame) : v;
       if (v != kReject) atomicOr(&rmask[ry + R * rz], (1u << rx) | ((same ? 1u : 0u) << (16 + rx)));
     }
     __syncthreads();
     if (ISO) {
-      for (int r = t; r < NR; r += NT) {
+      for (int q = t; q < NR; q += NT) {
+        const int r = q % R + RS * ((q / R) % R) + PS * (q / (R * R));
         const unsigned v = rv[r];
         rsc[r] = v != kReject ? __ldg(L.scal + (v & ~kSame)) : 0.f;
       }
@@ -1005,20 +1049,24 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
         if (!((emit[j] >> d) & 1u)) continue;
         const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
         unsigned v[8];
+        unsigned all_same = kSame;
         int cas = 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int r = c0[j] + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2));
+          const int r = c0[j] + (dx + (e & 1)) + RS * (dy + ((e >> 1) & 1)) + PS * (dz + (e >> 2));
+          all_same &= rv[r];
           v[e] = rv[r] & ~kSame;
           if (ISO) cas |= (rsc[r] > iso ? 1 : 0) << e;
         }
+        // 8 same-level cells at 8 positions are 8 different cells (kSame and
+        // kDistinct are the same bit)
         if (idx < cap) {   // written once, read much later: evict first
-          __stcs(duals + 2 * idx, make_uint4(v[0], v[1], v[2], v[3]));
+          __stcs(duals + 2 * idx, make_uint4(v[0] | all_same, v[1], v[2], v[3]));
           __stcs(duals + 2 * idx + 1, make_uint4(v[4], v[5], v[6], v[7]));
         }
         ++idx;
-        if (ISO && msh.count[cas]) ntri += __popc(kept_triangles(msh.packed[cas], msh.count[cas], v, mc.edge_a,
-                                                                 mc.edge_b));
+        if (ISO && msh.count[cas])
+          ntri += __popc(kept_of(all_same != 0, msh.packed[cas], msh.count[cas], v, mc.edge_a, mc.edge_b));
       }
     }
     if (ISO) {   // append this warp's triangles, then write them
@@ -1034,16 +1082,18 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
           const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
           unsigned v[8];
           float sv[8];
+          unsigned all_same = kSame;
           int cas = 0;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const int r = c0[j] + (dx + (e & 1)) + R * (dy + ((e >> 1) & 1)) + R * R * (dz + (e >> 2));
+            const int r = c0[j] + (dx + (e & 1)) + RS * (dy + ((e >> 1) & 1)) + PS * (dz + (e >> 2));
+            all_same &= rv[r];
             v[e] = rv[r] & ~kSame;
             sv[e] = rsc[r];
             cas |= (sv[e] > iso ? 1 : 0) << e;
           }
           if (!msh.count[cas]) continue;
-          const unsigned keep = kept_triangles(msh.packed[cas], msh.count[cas], v, mc.edge_a, mc.edge_b);
+          const unsigned keep = kept_of(all_same != 0, msh.packed[cas], msh.count[cas], v, mc.edge_a, mc.edge_b);
           if (!keep) continue;
           stage_row(vr, sr, v, sv);
           write_triangles<LOGB>(L.bricks, vr, sr, iso, msh.packed[cas], keep, tidx, tri_cap, tris, mc.edge_a,
@@ -1069,6 +1119,7 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
   __shared__ McShared sh;
   __shared__ unsigned row_v[EMIT ? 256 * kRow : 1];
   __shared__ float row_s[EMIT ? 256 * kRow : 1];
+  __shared__ float stage[EMIT ? 8 : 1][EMIT ? kTriStage * 9 : 1];   // per warp: its step's triangles
   load_mc(sh, mc);
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -1076,19 +1127,21 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   unsigned* vr = row_v + (EMIT ? threadIdx.x * kRow : 0);
   float* sr = row_s + (EMIT ? threadIdx.x * kRow : 0);
+  float* wst = stage[EMIT ? threadIdx.x >> 5 : 0];
   for (long long base = wid * 64; base < nd; base += nwarps * 64) {
     const long long d0 = base + lane, d1 = base + 32 + lane;
     const bool a0 = d0 < nd, a1 = d1 < nd;
     unsigned v0[8], v1[8];
     float s0[8], s1[8];
-    if (a0) load_dual(duals, d0, v0);
-    if (a1) load_dual(duals, d1, v1);
+    bool x0 = false, x1 = false;
+    if (a0) x0 = load_dual(duals, d0, v0);
+    if (a1) x1 = load_dual(duals, d1, v1);
     int c0 = 0, c1 = 0;
     if (a0) c0 = case_of(v0, s0, L.scal, iso);
     if (a1) c1 = case_of(v1, s1, L.scal, iso);
     unsigned k0 = 0, k1 = 0;
-    if (a0 && sh.count[c0]) k0 = kept_triangles(sh.packed[c0], sh.count[c0], v0, mc.edge_a, mc.edge_b);
-    if (a1 && sh.count[c1]) k1 = kept_triangles(sh.packed[c1], sh.count[c1], v1, mc.edge_a, mc.edge_b);
+    if (a0 && sh.count[c0]) k0 = kept_of(x0, sh.packed[c0], sh.count[c0], v0, mc.edge_a, mc.edge_b);
+    if (a1 && sh.count[c1]) k1 = kept_of(x1, sh.packed[c1], sh.count[c1], v1, mc.edge_a, mc.edge_b);
     if (CASES) {
       if (a0) {
         if (cases) cases[d0] = (unsigned char)c0;
@@ -1101,15 +1154,35 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
     }
     if (EMIT) {
       if (__ballot_sync(kFull, (k0 | k1) != 0) == 0) continue;
-      long long idx = warp_append(__popc(k0) + __popc(k1), counter);
-      if (k0) {
-        stage_row(vr, sr, v0, s0);
-        write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c0], k0, idx, cap, tris, mc.edge_a, mc.edge_b);
-        idx += __popc(k0);
-      }
-      if (k1) {
-        stage_row(vr, sr, v1, s1);
-        write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c1], k1, idx, cap, tris, mc.edge_a, mc.edge_b);
+      const unsigned mine = __popc(k0) + __popc(k1);
+      const unsigned total = __reduce_add_sync(kFull, mine);
+      long long idx = warp_append(mine, counter);
+      if (total <= (unsigned)kTriStage) {   // stage, then one coalesced run for the warp
+        const long long first = __shfl_sync(kFull, idx, 0);
+        float* out = wst + 9 * (idx - first);
+        if (k0) {
+          stage_row(vr, sr, v0, s0);
+          stage_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c0], k0, out, mc.edge_a, mc.edge_b);
+          out += 9 * __popc(k0);
+        }
+        if (k1) {
+          stage_row(vr, sr, v1, s1);
+          stage_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c1], k1, out, mc.edge_a, mc.edge_b);
+        }
+        __syncwarp();
+        const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
+        for (long long k = lane; k < lim; k += 32) tris[9 * first + k] = wst[k];
+        __syncwarp();
+      } else {
+        if (k0) {
+          stage_row(vr, sr, v0, s0);
+          write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c0], k0, idx, cap, tris, mc.edge_a, mc.edge_b);
+          idx += __popc(k0);
+        }
+        if (k1) {
+          stage_row(vr, sr, v1, s1);
+          write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c1], k1, idx, cap, tris, mc.edge_a, mc.edge_b);
+        }
       }
     }
   }
@@ -1135,7 +1208,7 @@ __global__ void __launch_bounds__(256) k_mc_batch_count(Locator L, const uint4* 
   for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < nd; d += stride) {
     unsigned v[8];
     float sv[8];
-    load_dual(duals, d, v);
+    const bool distinct = load_dual(duals, d, v);
     float mn = 3.4e38f, mx = -3.4e38f;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -1149,7 +1222,7 @@ __global__ void __launch_bounds__(256) k_mc_batch_count(Locator L, const uint4* 
       int cas = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) cas |= (sv[e] > iso ? 1 : 0) << e;
-      const unsigned keep = kept_triangles(sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
+      const unsigned keep = kept_of(distinct, sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
       if (keep) atomicAdd(&cnt_sh[k], (unsigned long long)__popc(keep));
     }
   }
@@ -1197,8 +1270,9 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
       float sv[8];
       float mn = 3.4e38f, mx = -3.4e38f;
       const bool live = d < t1;
+      bool distinct = false;
       if (live) {
-        load_dual(duals, d, v);
+        distinct = load_dual(duals, d, v);
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           sv[e] = __ldg(L.scal + v[e]);
@@ -1213,7 +1287,7 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
         if (live && mx > iso && !(mn > iso)) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) cas |= (sv[e] > iso ? 1 : 0) << e;
-          keep = kept_triangles(sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
+          keep = kept_of(distinct, sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
         }
         if (__ballot_sync(kFull, keep != 0) == 0) continue;
         const long long idx = warp_append(__popc(keep), &sc->n_tri[k]);
@@ -1250,8 +1324,9 @@ __global__ void __launch_bounds__(256) k_get_duals(const uint4* __restrict__ dua
                                                    int* __restrict__ out) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nd; i += stride) {
-    const uint4 a = __ldg(duals + i);
-    reinterpret_cast<int4*>(out)[i] = make_int4((int)__ldg(rec + a.x), (int)__ldg(rec + a.y),
+    const uint4 a = __ldg(duals + i);   // first word of a dual: kDistinct cleared
+    reinterpret_cast<int4*>(out)[i] = make_int4((int)__ldg(rec + ((i & 1) ? a.x : (a.x & ~kDistinct))),
+                                                (int)__ldg(rec + a.y),
                                                 (int)__ldg(rec + a.z), (int)__ldg(rec + a.w));
   }
 }
