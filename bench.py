@@ -55,13 +55,16 @@ WORKLOADS = {
 }
 
 
-def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int) -> float:
+def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int, placement: int = 0) -> float:
     """Compulsory bytes per launch of each kernel under the library's data
-    layout: what the kernel must read and write at least once."""
+    layout: what the kernel must read and write at least once. placement 2:
+    the insert pass records each cell's 4-byte table code and the coarse
+    binning reads it instead of the cell's corner and level."""
+    coded = placement == 2
     return {
-        "k_insert_bricks": 13.0 * n,                 # xyz + level
+        "k_insert_bricks": 13.0 * n + (4.0 * n if coded else 0.0),   # xyz + level (+ code)
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
-        "k_bin_coarse": 17.0 * n + 12.0 * n,         # read the cell, write a 12-byte entry
+        "k_bin_coarse": (8.0 if coded else 17.0) * n + 12.0 * n,   # read the cell, write a 12-byte entry
         "k_bin_fine": 12.0 * n + 12.0 * n,           # re-split the entries by window
         "k_place_windows": 12.0 * n + 8.0 * n_slots, # read the entries, write every slot's record
         "k_resolve_views": 16.0 * n_slots,           # read the record, write view + scalar
@@ -440,7 +443,7 @@ def main():
     kernels = {}
     for k, (tot_ms, cnt) in kt.items():
         per = tot_ms / cnt
-        b = algorithmic_bytes(k, n, inf.n_slots, nd, nt)
+        b = algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement)
         kernels[k] = {"ms_per_launch": per, "launches": cnt, "share": tot_ms / total_kms,
                       "algorithmic_bytes": b, "gbs": b / per / 1e6 if per > 0 else 0.0}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
@@ -452,7 +455,8 @@ def main():
                 "frac": dk["gbs"] / peak, "peak_source": peak_src,
                 "traffic": ncu_traffic(dom, args.workload, units),
                 "algorithmic_bytes_per_launch": dk["algorithmic_bytes"]}
-    step_bytes = sum(algorithmic_bytes(k, n, inf.n_slots, nd, nt) * v[1] / args.steps for k, v in kt.items())
+    step_bytes = sum(algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement) * v[1] / args.steps
+                     for k, v in kt.items())
 
     # batched multi-iso over the resident dual cells
     batch = None
@@ -542,6 +546,7 @@ def main():
             "config": {"workload": args.workload, "description": desc, "n_cells": n,
                        "step": "fused" if args.fused_iso else "dual_cells+iso",
                        "n_dual": nd, "n_triangles": nt, "iso": iso, "n_bricks": inf.n_bricks,
+                       "placement": ["direct", "binned", "binned+codes"][inf.placement],
                        "n_slots": inf.n_slots, "levels": inf.n_levels, "log2_brick": args.log2_brick,
                        "load_factor": args.load_factor, "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 ({(17 * n) / 1e6:.0f} MB of cells)"},

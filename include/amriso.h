@@ -180,8 +180,8 @@ int amr_iso_batch_async(amr_ctx* ctx, const float* d_isos, int n_iso,
 int amr_sync(amr_ctx* ctx);
 
 /* Frees the context's scratch workspace after waiting for its stream: the
- * staging of the binned cell placement (24 bytes per slot) and of host-
- * pointer delivery. The locator, the dual cells and the input stay; later
+ * staging of the binned cell placement (24 bytes per slot and 4 per cell)
+ * and of host-pointer delivery. The locator, the dual cells and the input stay; later
  * calls re-create the workspace on demand. No counterpart in the paper: a
  * memory-budget aid for keeping many data sets resident. */
 int amr_trim(amr_ctx* ctx);
@@ -193,7 +193,7 @@ const char* amr_strerror(int code);
  * of the build); a binding compares it with the header it was written for
  * and refuses a library built from other sources. No counterpart in the
  * paper. */
-#define AMR_ABI_VERSION 3
+#define AMR_ABI_VERSION 4
 int amr_abi_version(void);
 
 /* ---- introspection (host only, no device needed) ------------------------ */
@@ -215,6 +215,10 @@ typedef struct amr_info {
   int32_t n_levels;     /* max level + 1 */
   int32_t log2_brick;
   int64_t device_bytes; /* device memory held by the context */
+  int32_t placement;    /* how the last amr_build_locator placed the cells:
+                           0 direct scatter, 1 binned, 2 binned with each
+                           cell's table entry recorded by the insert pass */
+  int32_t reserved;
 } amr_info;
 int amr_get_info(amr_ctx* ctx, amr_info* info);
 

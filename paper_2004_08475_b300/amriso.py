@@ -59,10 +59,10 @@ class _Info(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int64), ("n_bricks", ctypes.c_int64),
                 ("n_slots", ctypes.c_int64), ("n_dual", ctypes.c_int64),
                 ("n_levels", ctypes.c_int32), ("log2_brick", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("placement", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-ABI_VERSION = 3   # AMR_ABI_VERSION of include/amriso.h
+ABI_VERSION = 4   # AMR_ABI_VERSION of include/amriso.h
 
 
 def _load() -> ctypes.CDLL:
@@ -153,6 +153,7 @@ class Info:
     n_levels: int
     log2_brick: int
     device_bytes: int
+    placement: int = 0   # 0 direct scatter, 1 binned, 2 binned with insert-pass codes
 
 
 class AmrContext:
@@ -319,7 +320,7 @@ class AmrContext:
         i = _Info()
         _check(_lib.amr_get_info(self._h, ctypes.byref(i)), "amr_get_info")
         return Info(i.n_cells, i.n_bricks, i.n_slots, i.n_dual, i.n_levels, i.log2_brick,
-                    i.device_bytes)
+                    i.device_bytes, i.placement)
 
     def enable_timing(self, on: bool = True):
         _check(_lib.amr_enable_timing(self._h, int(on)), "amr_enable_timing")

@@ -77,7 +77,8 @@ struct amr_ctx {
   float alpha = 0.5f;
   int block = 256;
   int check_overlap = 0;
-  DevBuf htab, bricks, rec, scal, view, nbr, staging;
+  DevBuf htab, bricks, rec, scal, view, nbr, staging, codes;
+  int placement = 0;   // 0 direct scatter, 1 binned, 2 binned with insert-pass codes
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
   int levels = 0;
@@ -292,7 +293,7 @@ void amr_destroy(amr_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
-                    &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->duals, &c->scratch,
+                    &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals, &c->scratch,
                     &c->stage_buf, &c->iso_buf, &c->seg_buf};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
@@ -322,6 +323,7 @@ int amr_trim(amr_ctx* c) {
   AMR_CUDA(cudaSetDevice(c->device));
   AMR_CUDA(cudaStreamSynchronize(c->stream));
   release(c->staging);
+  release(c->codes);
   release(c->stage_buf);
   return AMR_OK;
 }
@@ -385,8 +387,15 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   // it. A table that fills up stops the insert early and is rebuilt larger.
   unsigned long long want = (unsigned long long)((double)(n * 4 / B3 + 64) / alpha);
   want = std::min<unsigned long long>(want, 1ull << 22);
+  const bool binned = partitioned > 0 || (partitioned == 0 && n >= kBinnedMinCells);
+  unsigned* codes = nullptr;   // binned placement: each cell's table entry, recorded by the insert pass
   for (int attempt = 0;; ++attempt) {
     c->hcap = pow2_at_least(want);
+    codes = nullptr;
+    if (binned && n > 0 && c->hcap <= (1ull << (32 - 3 * logb))) {
+      AMR_TRY(ensure(c->codes, (size_t)n * 4));
+      codes = static_cast<unsigned*>(c->codes.p);
+    }
     const unsigned long long limit =
         (unsigned long long)((double)c->hcap * std::min(0.85, 2.0 * (double)alpha));
     AMR_TRY(ensure(c->htab, c->hcap * 16));
@@ -398,7 +407,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
       AMR_CUDA(launch_insert_bricks(logb, c->xyz, c->lvl, c->s, n,
                                     static_cast<ulonglong2*>(c->htab.p), c->hcap - 1,
                                     static_cast<int4*>(c->bricks.p), limit, dev_sc(c),
-                                    grid_for(c, n, block, 2048 / block), block, c->stream));
+                                    grid_for(c, n, block, 2048 / block), block, codes, c->stream));
     }
     AMR_TRY(read_scratch(c));
     const Scratch& h = *c->host_sc;
@@ -426,12 +435,13 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   if (c->n_slots) {
     const Locator L = make_locator(c);
     // binned placement unless asked otherwise or the input is small
-    if (partitioned > 0 || (partitioned == 0 && n >= kBinnedMinCells)) {
+    c->placement = binned ? (codes ? 2 : 1) : 0;
+    if (binned) {
       AMR_TRY(ensure(c->staging, bin_layout(c->n_slots).bytes));
       {
         KernelTimer kt(c, KT_BIN);
         AMR_CUDA(launch_bin_coarse(logb, c->xyz, c->lvl, c->s, n, L, c->n_slots, c->staging.p, dev_sc(c),
-                                   c->sm_count, c->stream));
+                                   c->sm_count, codes, c->stream));
       }
       {
         KernelTimer kt(c, KT_BIN_FINE);
@@ -704,8 +714,10 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->n_dual = c->stage >= 3 ? c->n_dual : -1;
   info->n_levels = c->stage >= 2 ? c->levels : 0;
   info->log2_brick = c->logb;
+  info->placement = c->placement;
+  info->reserved = 0;
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
-                          &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->duals,
+                          &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals,
                           &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);

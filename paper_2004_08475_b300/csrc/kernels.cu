@@ -116,7 +116,8 @@ template <int LOGB>
 __global__ void __launch_bounds__(1024) k_insert_bricks(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
     const float* __restrict__ s, long long n, ulonglong2* htab,
-    unsigned long long hmask, int4* bricks, unsigned long long brick_limit, Scratch* sc) {
+    unsigned long long hmask, int4* bricks, unsigned long long brick_limit, Scratch* sc,
+    unsigned* __restrict__ codes) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -170,6 +171,10 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
+      if (codes && lead[u] && cur[u] == key[u]) {   // found at its home entry
+        const long long i = base + u * 32 + lane;
+        __stcs(codes + i, ((unsigned)h[u] << (3 * LOGB)) | local_index<LOGB>(x[u], y[u], z[u], l[u]));
+      }
       if (!lead[u] || cur[u] == key[u]) continue;
       unsigned long long hh = h[u];
       bool done = false;
@@ -195,6 +200,10 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
         hh = (hh + 1) & hmask;
       }
       if (!done) err |= ERR_HASH_FULL;
+      if (codes && done) {   // the entry that holds the key stays put (no deletions)
+        const long long i = base + u * 32 + lane;
+        __stcs(codes + i, ((unsigned)hh << (3 * LOGB)) | local_index<LOGB>(x[u], y[u], z[u], l[u]));
+      }
     }
   }
   // block reduction, then one set of atomics per block
@@ -371,10 +380,14 @@ __device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gb
   return total;
 }
 
-template <int LOGB>
+// With codes (from k_insert_bricks: table entry << 3 LOGB | Morton index of
+// the cell in its brick), a cell's slot is one table read away; without,
+// the cell's key is formed and looked up again.
+template <int LOGB, bool CODED>
 __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl, const float* __restrict__ s,
-    long long n, Locator L, int n_coarse, Stage A, unsigned* __restrict__ coarse_count, Scratch* sc) {
+    long long n, Locator L, int n_coarse, Stage A, unsigned* __restrict__ coarse_count, Scratch* sc,
+    const unsigned* __restrict__ codes) {
   extern __shared__ unsigned smem[];
   unsigned* start = smem;                     // [kMaxCoarse] counts, then run starts in the tile
   unsigned* gbase = start + kMaxCoarse;       // [kMaxCoarse] run starts in the bins
@@ -388,8 +401,28 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
     for (int b = t; b < n_coarse; b += kBinThreads) start[b] = 0;
     __syncthreads();
     unsigned slot[kBinPerThread], rank[kBinPerThread], val[kBinPerThread];
+    if (CODED) {
 #pragma unroll
-    for (int h = 0; h < kBinPerThread; h += 4) {   // four cells at a time, first probes issued together
+      for (int j = 0; j < kBinPerThread; ++j) {
+        const long long i = tile0 + (long long)j * kBinThreads + t;
+        slot[j] = kReject;
+        rank[j] = 0;
+        val[j] = 0u;
+        if (i < n) {
+          const unsigned c = __ldcs(codes + i);
+          const float v = __ldcs(s + i);
+          if (!isfinite(v)) err |= ERR_NONFINITE;
+          val[j] = __float_as_uint(v);
+          const unsigned bi = (unsigned)__ldg(&L.htab[c >> (3 * LOGB)].y);
+          slot[j] = (bi << (3 * LOGB)) | (c & ((1u << (3 * LOGB)) - 1u));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kBinPerThread; ++j)
+        if (slot[j] != kReject) rank[j] = atomicAdd(&start[slot[j] >> kCoarseShift], 1u);
+    }
+#pragma unroll
+    for (int h = 0; h < (CODED ? 0 : kBinPerThread); h += 4) {   // four cells at a time, first probes together
       int loc[4];
       unsigned long long key[4], k0[4];
       int b0[4];
@@ -1106,28 +1139,36 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
   }
 }
 
+// Dynamic shared memory of k_mc<·, EMIT> per CTA of 256 threads: per warp
+// 64 rows (two duals per lane) of 8 vertex slots and 8 scalars, a list of
+// the step's kept triangles and their staged vertices.
+constexpr int kMcRowsWords = 8 * 64 * kRow;
+constexpr int kMcSmemBytes = 4 * (2 * kMcRowsWords + 8 * kTriStage + 8 * kTriStage * 9);
+
 // One lane per dual, two duals per lane per step: gather the 8 vertex
 // scalars, build the case index (bit e set iff s_e > iso), keep the case's
-// triangles that have three different edge keys, append them with one
-// atomic per warp and write their interpolated vertices. Optionally writes
-// per-dual case and triangle count instead.
+// triangles that have three different edge keys and append them with one
+// atomic per warp. The vertices are then computed lane-parallel: each lane
+// with triangles stages its duals' slots and scalars and lists its kept
+// triangles; the warp's 32 lanes take the step's 3T vertices in turn, stage
+// them, and write the step's triangles as one coalesced run. Optionally
+// writes per-dual case and triangle count instead.
 template <int LOGB, bool EMIT, bool CASES>
 __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
                                             float iso, float* __restrict__ tris, long long cap,
                                             unsigned long long* counter, unsigned char* cases,
                                             unsigned char* ntri, const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
-  __shared__ unsigned row_v[EMIT ? 256 * kRow : 1];
-  __shared__ float row_s[EMIT ? 256 * kRow : 1];
-  __shared__ float stage[EMIT ? 8 : 1][EMIT ? kTriStage * 9 : 1];   // per warp: its step's triangles
+  extern __shared__ __align__(16) unsigned mc_smem[];
   load_mc(sh, mc);
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  unsigned* vr = row_v + (EMIT ? threadIdx.x * kRow : 0);
-  float* sr = row_s + (EMIT ? threadIdx.x * kRow : 0);
-  float* wst = stage[EMIT ? threadIdx.x >> 5 : 0];
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+  unsigned* rows_v = mc_smem + w * 64 * kRow;                               // [64][kRow]
+  float* rows_s = reinterpret_cast<float*>(mc_smem + kMcRowsWords) + w * 64 * kRow;
+  unsigned* list = mc_smem + 2 * kMcRowsWords + w * kTriStage;             // [kTriStage]
+  float* wst = reinterpret_cast<float*>(mc_smem + 2 * kMcRowsWords + 8 * kTriStage) + w * kTriStage * 9;
   for (long long base = wid * 64; base < nd; base += nwarps * 64) {
     const long long d0 = base + lane, d1 = base + 32 + lane;
     const bool a0 = d0 < nd, a1 = d1 < nd;
@@ -1157,32 +1198,45 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
       const unsigned mine = __popc(k0) + __popc(k1);
       const unsigned total = __reduce_add_sync(kFull, mine);
       long long idx = warp_append(mine, counter);
-      if (total <= (unsigned)kTriStage) {   // stage, then one coalesced run for the warp
+      unsigned* r0 = rows_v + (2 * lane) * kRow;
+      float* q0 = rows_s + (2 * lane) * kRow;
+      if (k0) stage_row(r0, q0, v0, s0);
+      if (k1) stage_row(r0 + kRow, q0 + kRow, v1, s1);
+      if (total <= (unsigned)kTriStage) {
         const long long first = __shfl_sync(kFull, idx, 0);
-        float* out = wst + 9 * (idx - first);
-        if (k0) {
-          stage_row(vr, sr, v0, s0);
-          stage_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c0], k0, out, mc.edge_a, mc.edge_b);
-          out += 9 * __popc(k0);
-        }
-        if (k1) {
-          stage_row(vr, sr, v1, s1);
-          stage_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c1], k1, out, mc.edge_a, mc.edge_b);
+        unsigned pos = (unsigned)(idx - first);
+        const unsigned long long p0 = sh.packed[c0], p1 = sh.packed[c1];
+        for (int t = 0; t < 5; ++t)
+          if ((k0 >> t) & 1u) list[pos++] = (2u * lane) | ((unsigned)(p0 >> (12 * t)) & 0xFFFu) << 8;
+        for (int t = 0; t < 5; ++t)
+          if ((k1 >> t) & 1u) list[pos++] = (2u * lane + 1u) | ((unsigned)(p1 >> (12 * t)) & 0xFFFu) << 8;
+        __syncwarp();
+        for (unsigned q = lane; q < 3u * total; q += 32) {   // one vertex per lane
+          const unsigned e = q / 3u, c = q - 3u * e;
+          const unsigned ent = list[e];
+          const unsigned* rv = rows_v + (ent & 0xFFu) * kRow;
+          const float* rs = rows_s + (ent & 0xFFu) * kRow;
+          const int k = (int)((ent >> (8 + 4 * c)) & 15u);
+          const int a = (int)((mc.edge_a >> (4 * k)) & 15), b = (int)((mc.edge_b >> (4 * k)) & 15);
+          const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, rv[a]), rs[a], slot_cell<LOGB>(L.bricks, rv[b]),
+                                       rs[b], iso);
+          wst[3 * q] = p.x;
+          wst[3 * q + 1] = p.y;
+          wst[3 * q + 2] = p.z;
         }
         __syncwarp();
         const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
         for (long long k = lane; k < lim; k += 32) tris[9 * first + k] = wst[k];
         __syncwarp();
-      } else {
+      } else {   // more triangles than the stage holds: each lane writes its own
         if (k0) {
-          stage_row(vr, sr, v0, s0);
-          write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c0], k0, idx, cap, tris, mc.edge_a, mc.edge_b);
+          write_triangles<LOGB>(L.bricks, r0, q0, iso, sh.packed[c0], k0, idx, cap, tris, mc.edge_a, mc.edge_b);
           idx += __popc(k0);
         }
-        if (k1) {
-          stage_row(vr, sr, v1, s1);
-          write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[c1], k1, idx, cap, tris, mc.edge_a, mc.edge_b);
-        }
+        if (k1)
+          write_triangles<LOGB>(L.bricks, r0 + kRow, q0 + kRow, iso, sh.packed[c1], k1, idx, cap, tris, mc.edge_a,
+                                mc.edge_b);
+        __syncwarp();
       }
     }
   }
@@ -1352,9 +1406,9 @@ cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* 
                                  long long n, ulonglong2* htab,
                                  unsigned long long hmask, int4* bricks,
                                  unsigned long long brick_limit, Scratch* sc, int grid, int block,
-                                 cudaStream_t st) {
+                                 unsigned* codes, cudaStream_t st) {
   AMR_DISPATCH(logb, (k_insert_bricks<LB><<<grid, block, 0, st>>>(xyz, lvl, s, n, htab, hmask,
-                                                                   bricks, brick_limit, sc)));
+                                                                   bricks, brick_limit, sc, codes)));
   return cudaGetLastError();
 }
 
@@ -1400,32 +1454,39 @@ Stages stages_of(const BinLayout& lay, void* staging) {
 
 cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
                               Locator loc, long long n_slots, void* staging, Scratch* sc, int sm_count,
-                              cudaStream_t st) {
+                              const unsigned* codes, cudaStream_t st) {
   const BinLayout lay = bin_layout(n_slots);
   if (n_slots <= 0) return cudaSuccess;
   if (lay.n_coarse > kMaxCoarse || n > 0xFFFFFFFFll) return cudaErrorInvalidValue;
   const Stages S = stages_of(lay, staging);
   cudaError_t e = cudaMemsetAsync(S.coarse_count, 0, 4 * (size_t)(lay.n_coarse + lay.n_win), st);
   if (e != cudaSuccess) return e;
-  static bool attrs = false;   // dynamic shared memory above the 48 KB default: opt in once
-  if (!attrs) {
-    if ((e = cudaFuncSetAttribute(k_bin_coarse<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
-        (e = cudaFuncSetAttribute(k_bin_coarse<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
-        (e = cudaFuncSetAttribute(k_bin_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFine)) ||
-        (e = cudaFuncSetAttribute(k_place_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)))
-      return e;
-    attrs = true;
-  }
+  // dynamic shared memory above the 48 KB default (an attribute of the
+  // current device's context, so set on every build)
+  if ((e = cudaFuncSetAttribute(k_bin_coarse<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemCoarse)) ||
+      (e = cudaFuncSetAttribute(k_bin_coarse<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemCoarse)) ||
+      (e = cudaFuncSetAttribute(k_bin_coarse<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
+      (e = cudaFuncSetAttribute(k_bin_coarse<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
+      (e = cudaFuncSetAttribute(k_bin_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFine)) ||
+      (e = cudaFuncSetAttribute(k_place_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)))
+    return e;
   if (n <= 0) return cudaSuccess;
   const long long tiles = (n + kBinTile - 1) / kBinTile;
   AMR_DISPATCH(logb, ({
     int per_sm = 0;   // one resident wave: the tile loop is grid-strided
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_coarse<LB>, kBinThreads,
-                                                           kSmemCoarse)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+             &per_sm, codes ? k_bin_coarse<LB, true> : k_bin_coarse<LB, false>, kBinThreads, kSmemCoarse)) !=
+        cudaSuccess)
       return e;
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count * std::max(per_sm, 1));
-    k_bin_coarse<LB><<<grid, kBinThreads, kSmemCoarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse, S.a,
-                                                             S.coarse_count, sc);
+    if (codes)
+      k_bin_coarse<LB, true><<<grid, kBinThreads, kSmemCoarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse, S.a,
+                                                                     S.coarse_count, sc, codes);
+    else
+      k_bin_coarse<LB, false><<<grid, kBinThreads, kSmemCoarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse,
+                                                                      S.a, S.coarse_count, sc, nullptr);
   }));
   return cudaGetLastError();
 }
@@ -1490,8 +1551,15 @@ cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, f
     AMR_DISPATCH(logb, (k_mc<LB, false, true><<<grid, 256, 0, st>>>(loc, duals, nd, iso, tris, cap, counter,
                                                                      cases, ntri, mc)));
   } else {
-    AMR_DISPATCH(logb, (k_mc<LB, true, false><<<grid, 256, 0, st>>>(loc, duals, nd, iso, tris, cap, counter,
-                                                                     cases, ntri, mc)));
+    // dynamic shared memory above the 48 KB default (an attribute of the
+    // current device's context, so set on every launch)
+    AMR_DISPATCH(logb, ({
+      const cudaError_t e =
+          cudaFuncSetAttribute(k_mc<LB, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMcSmemBytes);
+      if (e != cudaSuccess) return e;
+      k_mc<LB, true, false><<<grid, 256, kMcSmemBytes, st>>>(loc, duals, nd, iso, tris, cap, counter, cases, ntri,
+                                                             mc);
+    }));
   }
   return cudaGetLastError();
 }

@@ -63,11 +63,14 @@ struct McConst {
 // brick_limit: once this many bricks exist the table counts as full
 // (ERR_HASH_FULL is raised and the remaining inserts stop early); bricks[]
 // must hold brick_limit entries. htab must be all ones before the launch.
+// codes (may be NULL; needs hcap << 3 log2_brick <= 2^32): per cell the
+// table entry of its brick << 3 log2_brick | its Morton index in the brick,
+// for launch_bin_coarse.
 cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
                                  long long n, ulonglong2* htab,
                                  unsigned long long hmask, int4* bricks,
                                  unsigned long long brick_limit, Scratch* sc, int grid, int block,
-                                 cudaStream_t st);
+                                 unsigned* codes, cudaStream_t st);
 
 // rec must be all ones (kEmptyRec) before the launch.
 cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* lvl, const float* s,
@@ -86,7 +89,7 @@ struct BinLayout {
 BinLayout bin_layout(long long n_slots);
 cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
                               Locator loc, long long n_slots, void* staging, Scratch* sc, int sm_count,
-                              cudaStream_t st);
+                              const unsigned* codes, cudaStream_t st);
 cudaError_t launch_bin_fine(long long n_slots, void* staging, Scratch* sc, cudaStream_t st);
 cudaError_t launch_place_windows(long long n_slots, void* staging, unsigned long long* rec, cudaStream_t st);
 

@@ -155,7 +155,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
   const int grid_cells = (int)std::max(1ll, std::min((long long)(n + block - 1) / block, (long long)sms * 8));
   if (n > 0)
     NA_TRY(rc_of(launch_insert_bricks(kLogB, xyz, level, scalar, n, htab, kHashCap - 1, bricks,
-                                      kMaxCells, sc, grid_cells, block, st)));
+                                      kMaxCells, sc, grid_cells, block, nullptr, st)));
   NA_TRY(read_counters(sc, &h, st));
   NA_TRY(err_bits(h.err));
   const long long n_bricks = (long long)h.n_bricks;
