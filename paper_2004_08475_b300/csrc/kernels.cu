@@ -32,12 +32,13 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// SplitMix64 output finaliser (Steele, Lea and Flood, "Fast splittable
-// pseudorandom number generators", 2014), used as the bucket hash.
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
+// Home entry of a key: Fibonacci (multiplicative) hashing (Knuth, The Art
+// of Computer Programming vol. 3, Sec. 6.4), the top log2(hcap) bits of
+// key * 2^64/phi, rounded down to an even entry so that the first probe
+// reads one 32-byte sector of two entries. Probing is linear from there.
+// hcap >= 2.
+__device__ __forceinline__ unsigned long long home_of(unsigned long long key, unsigned long long hmask) {
+  return ((key * 0x9E3779B97F4A7C15ull) >> (64 - __popcll(hmask))) & ~1ull;
 }
 
 // Key of the level-l brick containing finest-level point (x,y,z). Brick
@@ -52,12 +53,12 @@ __device__ __forceinline__ unsigned long long brick_key(int x, int y, int z, int
   return ((unsigned long long)l << 60) | (bz << 40) | (by << 20) | bx;
 }
 
+// Bits b of v (v < 2^LOGB) moved to bit 3b.
 template <int LOGB>
 __device__ __forceinline__ unsigned spread(unsigned v) {
-  unsigned r = 0;
-#pragma unroll
-  for (int b = 0; b < LOGB; ++b) r |= ((v >> b) & 1u) << (3 * b);
-  return r;
+  static_assert(LOGB == 2 || LOGB == 3, "bricks of 4^3 or 8^3 cells");
+  if constexpr (LOGB == 3) return (v | (v << 2) | (v << 4)) & 0x49u;
+  else return (v | (v << 2)) & 0x9u;
 }
 
 template <int LOGB>
@@ -78,14 +79,28 @@ __device__ __forceinline__ unsigned local_index(int x, int y, int z, int l) {
 }
 
 __device__ __forceinline__ int find_brick(const Locator& L, unsigned long long key) {
-  unsigned long long h = mix64(key) & L.hmask;
-  for (unsigned long long p = 0; p <= L.hmask; ++p) {
-    const ulonglong2 e = __ldg(L.htab + h);
-    if (e.x == key) return (int)e.y;
-    if (e.x == kEmptyKey) return -1;
-    h = (h + 1) & L.hmask;
+  unsigned long long h = home_of(key, L.hmask);
+  for (unsigned long long p = 0; p <= L.hmask; p += 2) {   // one sector (two entries) per step
+    const ulonglong2 e0 = __ldg(L.htab + h), e1 = __ldg(L.htab + h + 1);
+    if (e0.x == key) return (int)e0.y;
+    if (e0.x == kEmptyKey) return -1;
+    if (e1.x == key) return (int)e1.y;
+    if (e1.x == kEmptyKey) return -1;
+    h = (h + 2) & L.hmask;
   }
   return -1;
+}
+
+// First probe, for callers that issue several at once: the key's home
+// sector; returns the brick index, or -2 when the key lies further on.
+__device__ __forceinline__ int probe_home(const Locator& L, unsigned long long key) {
+  const unsigned long long h = home_of(key, L.hmask);
+  const ulonglong2 e0 = __ldg(L.htab + h), e1 = __ldg(L.htab + h + 1);
+  if (e0.x == key) return (int)e0.y;
+  if (e0.x == kEmptyKey) return -1;
+  if (e1.x == key) return (int)e1.y;
+  if (e1.x == kEmptyKey) return -1;
+  return -2;
 }
 
 // Lower corner and level of the cell stored in `slot`.
@@ -143,7 +158,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
         l[u] = __ldcs(lvl + i);
       }
     }
-    unsigned long long key[kUnroll], h[kUnroll], cur[kUnroll];
+    unsigned long long key[kUnroll], h[kUnroll], cur[kUnroll], cur1[kUnroll];
     bool lead[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -166,16 +181,19 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
         }
       }
       lead[u] = key[u] != kEmptyKey;
-      h[u] = mix64(key[u]) & hmask;
-      cur[u] = lead[u] ? __ldcg(&htab[h[u]].x) : 0ull;   // independent first probes
+      h[u] = home_of(key[u], hmask);
+      cur[u] = lead[u] ? __ldcg(&htab[h[u]].x) : 0ull;   // independent first probes: the home sector
+      cur1[u] = lead[u] ? __ldcg(&htab[h[u] + 1].x) : 0ull;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      if (codes && lead[u] && cur[u] == key[u]) {   // found at its home entry
+      const bool home = cur[u] == key[u] || cur1[u] == key[u];
+      if (codes && lead[u] && home) {   // found in its home sector
         const long long i = base + u * 32 + lane;
-        __stcs(codes + i, ((unsigned)h[u] << (3 * LOGB)) | local_index<LOGB>(x[u], y[u], z[u], l[u]));
+        const unsigned e = (unsigned)h[u] + (cur[u] == key[u] ? 0u : 1u);
+        __stcs(codes + i, (e << (3 * LOGB)) | local_index<LOGB>(x[u], y[u], z[u], l[u]));
       }
-      if (!lead[u] || cur[u] == key[u]) continue;
+      if (!lead[u] || home) continue;
       unsigned long long hh = h[u];
       bool done = false;
       for (unsigned long long p = 0; p < limit; ++p) {
@@ -282,20 +300,17 @@ __global__ void __launch_bounds__(1024) k_scatter_cells(
         if (!isfinite(v[u])) err |= ERR_NONFINITE;
       }
     }
-    unsigned long long key[kUnroll], k0[kUnroll];
+    unsigned long long key[kUnroll];
     int b0[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {   // first probe of every key, issued together
       key[u] = (l[u] >= 0 && l[u] <= kMaxLevel) ? brick_key<LOGB>(x[u], y[u], z[u], l[u]) : kEmptyKey;
-      const unsigned long long h = mix64(key[u]) & L.hmask;
-      const ulonglong2 e = key[u] != kEmptyKey ? __ldg(L.htab + h) : make_ulonglong2(kEmptyKey, ~0ull);
-      k0[u] = e.x;
-      b0[u] = (int)e.y;
+      b0[u] = key[u] != kEmptyKey ? probe_home(L, key[u]) : -1;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       if (key[u] == kEmptyKey) continue;
-      const int bi = k0[u] == key[u] ? b0[u] : find_brick(L, key[u]);
+      const int bi = b0[u] != -2 ? b0[u] : find_brick(L, key[u]);
       if (bi < 0) {
         err |= ERR_HASH_FULL;
         continue;
@@ -424,7 +439,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
 #pragma unroll
     for (int h = 0; h < (CODED ? 0 : kBinPerThread); h += 4) {   // four cells at a time, first probes together
       int loc[4];
-      unsigned long long key[4], k0[4];
+      unsigned long long key[4];
       int b0[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -443,17 +458,14 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
             loc[u] = (int)local_index<LOGB>(x, y, z, l);
           }
         }
-        const unsigned long long hh = mix64(key[u]) & L.hmask;
-        const ulonglong2 e = key[u] != kEmptyKey ? __ldg(L.htab + hh) : make_ulonglong2(kEmptyKey, ~0ull);
-        k0[u] = e.x;
-        b0[u] = (int)e.y;
+        b0[u] = key[u] != kEmptyKey ? probe_home(L, key[u]) : -1;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         slot[h + u] = kReject;
         rank[h + u] = 0;
         if (key[u] == kEmptyKey) continue;
-        const int bi = k0[u] == key[u] ? b0[u] : find_brick(L, key[u]);
+        const int bi = b0[u] != -2 ? b0[u] : find_brick(L, key[u]);
         if (bi < 0) {
           err |= ERR_HASH_FULL;
           continue;
