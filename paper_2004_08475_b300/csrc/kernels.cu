@@ -159,10 +159,12 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
       }
     }
     unsigned long long key[kUnroll], h[kUnroll], cur[kUnroll], cur1[kUnroll];
+    unsigned loc[kUnroll];
     bool lead[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       key[u] = kEmptyKey;
+      loc[u] = 0;
       if (l[u] >= 0) {
         if (l[u] > kMaxLevel) {
           err |= ERR_RANGE;
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
           hi2 = max(hi2, (int)min((long long)z[u] + w, (long long)INT_MAX));
           ml = max(ml, l[u]);
           key[u] = brick_key<LOGB>(x[u], y[u], z[u], l[u]);
+          loc[u] = local_index<LOGB>(x[u], y[u], z[u], l[u]);
         }
       }
       lead[u] = key[u] != kEmptyKey;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
       if (codes && lead[u] && home) {   // found in its home sector
         const long long i = base + u * 32 + lane;
         const unsigned e = (unsigned)h[u] + (cur[u] == key[u] ? 0u : 1u);
-        __stcs(codes + i, (e << (3 * LOGB)) | local_index<LOGB>(x[u], y[u], z[u], l[u]));
+        __stcs(codes + i, (e << (3 * LOGB)) | loc[u]);
       }
       if (!lead[u] || home) continue;
       unsigned long long hh = h[u];
@@ -204,9 +207,11 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
           if (prev == kEmptyKey) {
             const unsigned long long bi = atomicAdd(&sc->n_bricks, 1ull);
             htab[hh].y = bi;
-            if (bi < brick_limit) {   // bricks[] holds brick_limit entries
-              const int m = ~((1 << (l[u] + LOGB)) - 1);
-              bricks[bi] = make_int4(x[u] & m, y[u] & m, z[u] & m, l[u]);
+            if (bi < brick_limit) {   // bricks[] holds brick_limit entries; the cell is read again
+              const long long i = base + u * 32 + lane;
+              const int lv = lvl[i];
+              const int m = ~((1 << (lv + LOGB)) - 1);
+              bricks[bi] = make_int4(xyz[3 * i] & m, xyz[3 * i + 1] & m, xyz[3 * i + 2] & m, lv);
             } else {
               atomicOr(&sc->err, (unsigned)ERR_HASH_FULL);
             }
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
       if (!done) err |= ERR_HASH_FULL;
       if (codes && done) {   // the entry that holds the key stays put (no deletions)
         const long long i = base + u * 32 + lane;
-        __stcs(codes + i, ((unsigned)hh << (3 * LOGB)) | local_index<LOGB>(x[u], y[u], z[u], l[u]));
+        __stcs(codes + i, ((unsigned)hh << (3 * LOGB)) | loc[u]);
       }
     }
   }
@@ -969,8 +974,11 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
   __shared__ unsigned long long cta_base;
   __shared__ float rsc[ISO ? NP : 1];                 // scalars of the region's cells
   __shared__ McShared msh;
-  __shared__ unsigned row_v[ISO ? NT * kRow : 1];
-  __shared__ float row_s[ISO ? NT * kRow : 1];
+  // ISO: per warp the step's triangle list and staged vertices (the stage
+  // doubles as the warp's per-thread rows when the list overflows)
+  __shared__ unsigned tlist[ISO ? NW : 1][ISO ? kTriStage : 1];
+  __shared__ __align__(16) float tstage[ISO ? NW : 1][ISO ? kTriStage * 9 : 1];
+  static_assert(!ISO || 32 * 2 * kRow <= kTriStage * 9, "fallback rows fit the stage");
   const int t = threadIdx.x;
   const int lane = t & 31, wp = t >> 5;
   if (ISO) {
@@ -1114,38 +1122,94 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
           ntri += __popc(kept_of(all_same != 0, msh.packed[cas], msh.count[cas], v, mc.edge_a, mc.edge_b));
       }
     }
-    if (ISO) {   // append this warp's triangles, then write them
+    if (ISO) {   // append this warp's triangles, then compute their vertices lane-parallel
       long long tidx = warp_append(ntri, &sc->n_tri[0]);
-      unsigned* vr = row_v + t * kRow;
-      float* sr = row_s + t * kRow;
+      const unsigned total = __reduce_add_sync(kFull, ntri);
+      const long long first = __shfl_sync(kFull, tidx, 0);
+      float* wst = tstage[wp];
+      unsigned* lst = tlist[wp];
+      if (total <= (unsigned)kTriStage) {
+        unsigned pos = (unsigned)(tidx - first);
 #pragma unroll 1
-      for (int j = 0; j < CPT; ++j) {
-        if (!ntri) break;
+        for (int j = 0; j < CPT; ++j) {
+          if (!ntri) break;
 #pragma unroll 1
-        for (int d = 0; d < 8; ++d) {
-          if (!((emit[j] >> d) & 1u)) continue;
-          const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
-          unsigned v[8];
-          float sv[8];
-          unsigned all_same = kSame;
-          int cas = 0;
+          for (int d = 0; d < 8; ++d) {
+            if (!((emit[j] >> d) & 1u)) continue;
+            const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+            unsigned v[8];
+            unsigned all_same = kSame;
+            int cas = 0;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int r = c0[j] + (dx + (e & 1)) + RS * (dy + ((e >> 1) & 1)) + PS * (dz + (e >> 2));
-            all_same &= rv[r];
-            v[e] = rv[r] & ~kSame;
-            sv[e] = rsc[r];
-            cas |= (sv[e] > iso ? 1 : 0) << e;
+            for (int e = 0; e < 8; ++e) {
+              const int r = c0[j] + (dx + (e & 1)) + RS * (dy + ((e >> 1) & 1)) + PS * (dz + (e >> 2));
+              all_same &= rv[r];
+              v[e] = rv[r] & ~kSame;
+              cas |= (rsc[r] > iso ? 1 : 0) << e;
+            }
+            if (!msh.count[cas]) continue;
+            const unsigned long long pk = msh.packed[cas];
+            const unsigned keep = kept_of(all_same != 0, pk, msh.count[cas], v, mc.edge_a, mc.edge_b);
+            for (int tt = 0; tt < 5; ++tt)   // entry: source lane, cell j, dual d, the triangle's 3 edges
+              if ((keep >> tt) & 1u)
+                lst[pos++] = (unsigned)lane | ((unsigned)j << 5) | ((unsigned)d << 6) |
+                             (((unsigned)(pk >> (12 * tt)) & 0xFFFu) << 9);
           }
-          if (!msh.count[cas]) continue;
-          const unsigned keep = kept_of(all_same != 0, msh.packed[cas], msh.count[cas], v, mc.edge_a, mc.edge_b);
-          if (!keep) continue;
-          stage_row(vr, sr, v, sv);
-          write_triangles<LOGB>(L.bricks, vr, sr, iso, msh.packed[cas], keep, tidx, tri_cap, tris, mc.edge_a,
-                                mc.edge_b);
-          tidx += __popc(keep);
+        }
+        __syncwarp();
+        for (unsigned q = lane; q < 3u * total; q += 32) {   // one vertex per lane
+          const unsigned e = q / 3u, c = q - 3u * e;
+          const unsigned ent = lst[e];
+          const int m = wp * 32 + (int)(ent & 31u) + (int)((ent >> 5) & 1u) * NT;   // the source cell
+          const int d = (int)((ent >> 6) & 7u);
+          const int cb = compact<LOGB>(m) + (d & 1) + RS * (compact<LOGB>(m >> 1) + ((d >> 1) & 1)) +
+                         PS * (compact<LOGB>(m >> 2) + (d >> 2));
+          const int k = (int)((ent >> (9 + 4 * c)) & 15u);
+          const int a = (int)((mc.edge_a >> (4 * k)) & 15), b = (int)((mc.edge_b >> (4 * k)) & 15);
+          const int ra = cb + (a & 1) + RS * ((a >> 1) & 1) + PS * (a >> 2);
+          const int rb = cb + (b & 1) + RS * ((b >> 1) & 1) + PS * (b >> 2);
+          const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, rv[ra] & ~kSame), rsc[ra],
+                                       slot_cell<LOGB>(L.bricks, rv[rb] & ~kSame), rsc[rb], iso);
+          wst[3 * q] = p.x;
+          wst[3 * q + 1] = p.y;
+          wst[3 * q + 2] = p.z;
+        }
+        __syncwarp();
+        const long long lim = min((long long)total, tri_cap - first) * 9;   // capacity: exact prefix only
+        for (long long k = lane; k < lim; k += 32) tris[9 * first + k] = wst[k];
+      } else {   // more triangles than the stage holds: each thread writes its own
+        unsigned* vr = reinterpret_cast<unsigned*>(wst) + lane * 2 * kRow;
+        float* sr = wst + lane * 2 * kRow + kRow;
+#pragma unroll 1
+        for (int j = 0; j < CPT; ++j) {
+          if (!ntri) break;
+#pragma unroll 1
+          for (int d = 0; d < 8; ++d) {
+            if (!((emit[j] >> d) & 1u)) continue;
+            const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+            unsigned v[8];
+            float sv[8];
+            unsigned all_same = kSame;
+            int cas = 0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int r = c0[j] + (dx + (e & 1)) + RS * (dy + ((e >> 1) & 1)) + PS * (dz + (e >> 2));
+              all_same &= rv[r];
+              v[e] = rv[r] & ~kSame;
+              sv[e] = rsc[r];
+              cas |= (sv[e] > iso ? 1 : 0) << e;
+            }
+            if (!msh.count[cas]) continue;
+            const unsigned keep = kept_of(all_same != 0, msh.packed[cas], msh.count[cas], v, mc.edge_a, mc.edge_b);
+            if (!keep) continue;
+            stage_row(vr, sr, v, sv);
+            write_triangles<LOGB>(L.bricks, vr, sr, iso, msh.packed[cas], keep, tidx, tri_cap, tris, mc.edge_a,
+                                  mc.edge_b);
+            tidx += __popc(keep);
+          }
         }
       }
+      __syncwarp();
     }
     __syncthreads();
   }
@@ -1210,18 +1274,18 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
       const unsigned mine = __popc(k0) + __popc(k1);
       const unsigned total = __reduce_add_sync(kFull, mine);
       long long idx = warp_append(mine, counter);
-      unsigned* r0 = rows_v + (2 * lane) * kRow;
-      float* q0 = rows_s + (2 * lane) * kRow;
+      unsigned* r0 = rows_v + lane * kRow;   // rows lane and 32 + lane: conflict-free
+      float* q0 = rows_s + lane * kRow;
       if (k0) stage_row(r0, q0, v0, s0);
-      if (k1) stage_row(r0 + kRow, q0 + kRow, v1, s1);
+      if (k1) stage_row(r0 + 32 * kRow, q0 + 32 * kRow, v1, s1);
       if (total <= (unsigned)kTriStage) {
         const long long first = __shfl_sync(kFull, idx, 0);
         unsigned pos = (unsigned)(idx - first);
         const unsigned long long p0 = sh.packed[c0], p1 = sh.packed[c1];
         for (int t = 0; t < 5; ++t)
-          if ((k0 >> t) & 1u) list[pos++] = (2u * lane) | ((unsigned)(p0 >> (12 * t)) & 0xFFFu) << 8;
+          if ((k0 >> t) & 1u) list[pos++] = (unsigned)lane | ((unsigned)(p0 >> (12 * t)) & 0xFFFu) << 8;
         for (int t = 0; t < 5; ++t)
-          if ((k1 >> t) & 1u) list[pos++] = (2u * lane + 1u) | ((unsigned)(p1 >> (12 * t)) & 0xFFFu) << 8;
+          if ((k1 >> t) & 1u) list[pos++] = (32u + lane) | ((unsigned)(p1 >> (12 * t)) & 0xFFFu) << 8;
         __syncwarp();
         for (unsigned q = lane; q < 3u * total; q += 32) {   // one vertex per lane
           const unsigned e = q / 3u, c = q - 3u * e;
@@ -1246,8 +1310,8 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
           idx += __popc(k0);
         }
         if (k1)
-          write_triangles<LOGB>(L.bricks, r0 + kRow, q0 + kRow, iso, sh.packed[c1], k1, idx, cap, tris, mc.edge_a,
-                                mc.edge_b);
+          write_triangles<LOGB>(L.bricks, r0 + 32 * kRow, q0 + 32 * kRow, iso, sh.packed[c1], k1, idx, cap, tris,
+                                mc.edge_a, mc.edge_b);
         __syncwarp();
       }
     }
