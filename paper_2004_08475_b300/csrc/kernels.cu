@@ -350,9 +350,12 @@ constexpr int kMaxCoarse = 1 << (31 - kCoarseShift);   // slot indices stay belo
 constexpr int kWinShift = 13;
 constexpr int kWinSlots = 1 << kWinShift;
 constexpr int kFinePerCoarse = 1 << (kCoarseShift - kWinShift);
-constexpr int kBinThreads = 512;
-constexpr int kBinPerThread = 8;
-constexpr int kBinTile = kBinThreads * kBinPerThread;
+constexpr int kCoarseThreads = 512;
+constexpr int kCoarsePer = 8;
+constexpr int kCoarseTile = kCoarseThreads * kCoarsePer;
+constexpr int kFineThreads = 256;   // five CTAs per SM: their barriers overlap
+constexpr int kFinePer = 8;
+constexpr int kFineTile = kFineThreads * kFinePer;
 constexpr int kPlaceThreads = 512;
 
 struct Stage {
@@ -361,17 +364,22 @@ struct Stage {
   unsigned* val;
 };
 
-// Exclusive scan of cnt[0..m) in place (m <= 2 * blockDim.x) and, for every
-// non-empty entry, a run reserved in the global counter gcount[goff + b];
-// returns the total. All threads of the CTA must call it.
+// Exclusive scan of cnt[0..m) in place (m <= PER * blockDim.x) and, for
+// every non-empty entry, a run reserved in the global counter gcount[goff +
+// b]; returns the total. All threads of the CTA must call it.
+template <int PER>
 __device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gbase, int m,
                                                      unsigned* gcount, long long goff, unsigned* wsum) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
-  const int b0 = 2 * t, b1 = 2 * t + 1;
-  const unsigned c0 = b0 < m ? cnt[b0] : 0u, c1 = b1 < m ? cnt[b1] : 0u;
-  if (c0) gbase[b0] = atomicAdd(gcount + goff + b0, c0);
-  if (c1) gbase[b1] = atomicAdd(gcount + goff + b1, c1);
-  const unsigned v = c0 + c1;
+  unsigned c[PER];
+  unsigned v = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int b = PER * t + k;
+    c[k] = b < m ? cnt[b] : 0u;
+    if (c[k]) gbase[b] = atomicAdd(gcount + goff + b, c[k]);
+    v += c[k];
+  }
   unsigned incl = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -382,19 +390,23 @@ __device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gb
   __syncthreads();
   if (w == 0) {
     const unsigned x = lane < nw ? wsum[lane] : 0u;
-    unsigned c = x;
+    unsigned cc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, c, o);
-      if (lane >= o) c += y;
+      const unsigned y = __shfl_up_sync(kFull, cc, o);
+      if (lane >= o) cc += y;
     }
-    if (lane < nw) wsum[lane] = c - x;
-    if (lane == 31) wsum[32] = c;
+    if (lane < nw) wsum[lane] = cc - x;
+    if (lane == 31) wsum[32] = cc;
   }
   __syncthreads();
-  const unsigned ex = wsum[w] + incl - v;
-  if (b0 < m) cnt[b0] = ex;
-  if (b1 < m) cnt[b1] = ex + c0;
+  unsigned ex = wsum[w] + incl - v;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int b = PER * t + k;
+    if (b < m) cnt[b] = ex;
+    ex += c[k];
+  }
   const unsigned total = wsum[32];
   __syncthreads();
   return total;
@@ -404,27 +416,28 @@ __device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gb
 // the cell in its brick), a cell's slot is one table read away; without,
 // the cell's key is formed and looked up again.
 template <int LOGB, bool CODED>
-__global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
+__global__ void __launch_bounds__(kCoarseThreads) k_bin_coarse(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl, const float* __restrict__ s,
     long long n, Locator L, int n_coarse, Stage A, unsigned* __restrict__ coarse_count, Scratch* sc,
     const unsigned* __restrict__ codes) {
   extern __shared__ unsigned smem[];
-  unsigned* start = smem;                     // [kMaxCoarse] counts, then run starts in the tile
-  unsigned* gbase = start + kMaxCoarse;       // [kMaxCoarse] run starts in the bins
-  unsigned* t_slot = gbase + kMaxCoarse;      // [kBinTile] the tile sorted by bin
-  unsigned* t_idx = t_slot + kBinTile;
-  unsigned* t_val = t_idx + kBinTile;
+  unsigned* start = smem;                     // [n_coarse] counts, then run starts in the tile
+  unsigned* gbase = start + n_coarse;         // [n_coarse] run starts in the bins
+  unsigned* t_slot = gbase + n_coarse;        // [kCoarseTile] the tile sorted by bin
+  unsigned* t_idx = t_slot + kCoarseTile;
+  unsigned* t_val = t_idx + kCoarseTile;
   __shared__ unsigned wsum[33];
   const int t = threadIdx.x, lane = t & 31;
   unsigned err = 0;
-  for (long long tile0 = (long long)blockIdx.x * kBinTile; tile0 < n; tile0 += (long long)gridDim.x * kBinTile) {
-    for (int b = t; b < n_coarse; b += kBinThreads) start[b] = 0;
+  for (long long tile0 = (long long)blockIdx.x * kCoarseTile; tile0 < n;
+       tile0 += (long long)gridDim.x * kCoarseTile) {
+    for (int b = t; b < n_coarse; b += kCoarseThreads) start[b] = 0;
     __syncthreads();
-    unsigned slot[kBinPerThread], rank[kBinPerThread], val[kBinPerThread];
+    unsigned slot[kCoarsePer], rank[kCoarsePer], val[kCoarsePer];
     if (CODED) {
 #pragma unroll
-      for (int j = 0; j < kBinPerThread; ++j) {
-        const long long i = tile0 + (long long)j * kBinThreads + t;
+      for (int j = 0; j < kCoarsePer; ++j) {
+        const long long i = tile0 + (long long)j * kCoarseThreads + t;
         slot[j] = kReject;
         rank[j] = 0;
         val[j] = 0u;
@@ -438,17 +451,17 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
         }
       }
 #pragma unroll
-      for (int j = 0; j < kBinPerThread; ++j)
+      for (int j = 0; j < kCoarsePer; ++j)
         if (slot[j] != kReject) rank[j] = atomicAdd(&start[slot[j] >> kCoarseShift], 1u);
     }
 #pragma unroll
-    for (int h = 0; h < (CODED ? 0 : kBinPerThread); h += 4) {   // four cells at a time, first probes together
+    for (int h = 0; h < (CODED ? 0 : kCoarsePer); h += 4) {   // four cells at a time, first probes together
       int loc[4];
       unsigned long long key[4];
       int b0[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const long long i = tile0 + (long long)(h + u) * kBinThreads + t;
+        const long long i = tile0 + (long long)(h + u) * kCoarseThreads + t;
         key[u] = kEmptyKey;
         loc[u] = 0;
         val[h + u] = 0u;
@@ -480,17 +493,18 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
       }
     }
     __syncthreads();
-    const unsigned total = scan_and_reserve(start, gbase, n_coarse, coarse_count, 0, wsum);
+    const unsigned total = scan_and_reserve<kMaxCoarse / kCoarseThreads>(start, gbase, n_coarse, coarse_count, 0,
+                                                                         wsum);
 #pragma unroll
-    for (int j = 0; j < kBinPerThread; ++j) {
+    for (int j = 0; j < kCoarsePer; ++j) {
       if (slot[j] == kReject) continue;
       const unsigned pos = start[slot[j] >> kCoarseShift] + rank[j];
       t_slot[pos] = slot[j];
-      t_idx[pos] = (unsigned)(tile0 + (long long)j * kBinThreads + t);
+      t_idx[pos] = (unsigned)(tile0 + (long long)j * kCoarseThreads + t);
       t_val[pos] = val[j];
     }
     __syncthreads();
-    for (unsigned p = t; p < total; p += kBinThreads) {   // runs of one bin are contiguous: coalesced
+    for (unsigned p = t; p < total; p += kCoarseThreads) {   // runs of one bin are contiguous: coalesced
       const unsigned sl = t_slot[p];
       const unsigned b = sl >> kCoarseShift;
       const unsigned r = gbase[b] + (p - start[b]);
@@ -510,31 +524,31 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_coarse(
 }
 
 // Grid (tiles of one coarse bin, coarse bins).
-__global__ void __launch_bounds__(kBinThreads) k_bin_fine(Stage A, const unsigned* __restrict__ coarse_count,
+__global__ void __launch_bounds__(kFineThreads) k_bin_fine(Stage A, const unsigned* __restrict__ coarse_count,
                                                           Stage B, unsigned* __restrict__ win_count, Scratch* sc) {
   extern __shared__ unsigned smem[];
   unsigned* start = smem;                      // [kFinePerCoarse]
   unsigned* gbase = start + kFinePerCoarse;    // [kFinePerCoarse]
-  unsigned* t_slot = gbase + kFinePerCoarse;   // [kBinTile]
-  unsigned* t_idx = t_slot + kBinTile;
-  unsigned* t_val = t_idx + kBinTile;
+  unsigned* t_slot = gbase + kFinePerCoarse;   // [kFineTile]
+  unsigned* t_idx = t_slot + kFineTile;
+  unsigned* t_val = t_idx + kFineTile;
   __shared__ unsigned wsum[33];
   const int t = threadIdx.x;
   const long long cb = blockIdx.y;
   const unsigned cnt = min(__ldg(coarse_count + cb), 1u << kCoarseShift);
-  const unsigned tile0 = blockIdx.x * (unsigned)kBinTile;
+  const unsigned tile0 = blockIdx.x * (unsigned)kFineTile;
   if (tile0 >= cnt) return;   // uniform over the CTA
-  for (int b = t; b < kFinePerCoarse; b += kBinThreads) start[b] = 0;
+  for (int b = t; b < kFinePerCoarse; b += kFineThreads) start[b] = 0;
   __syncthreads();
-  unsigned slot[kBinPerThread], rank[kBinPerThread], idx[kBinPerThread], val[kBinPerThread];
+  unsigned slot[kFinePer], rank[kFinePer], idx[kFinePer], val[kFinePer];
   const long long src0 = (cb << kCoarseShift) + tile0;
 #pragma unroll
-  for (int j = 0; j < kBinPerThread; ++j) {
-    const unsigned e = tile0 + j * kBinThreads + t;
+  for (int j = 0; j < kFinePer; ++j) {
+    const unsigned e = tile0 + j * kFineThreads + t;
     slot[j] = kReject;
     rank[j] = 0;
     if (e < cnt) {
-      const long long src = src0 + j * kBinThreads + t;
+      const long long src = src0 + j * kFineThreads + t;
       slot[j] = __ldcs(A.slot + src);
       idx[j] = __ldcs(A.idx + src);
       val[j] = __ldcs(A.val + src);
@@ -542,10 +556,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_fine(Stage A, const unsigne
     }
   }
   __syncthreads();
-  const unsigned total = scan_and_reserve(start, gbase, kFinePerCoarse, win_count, cb << (kCoarseShift - kWinShift),
-                                          wsum);
+  const unsigned total = scan_and_reserve<kFinePerCoarse / kFineThreads>(start, gbase, kFinePerCoarse, win_count,
+                                                                         cb << (kCoarseShift - kWinShift), wsum);
 #pragma unroll
-  for (int j = 0; j < kBinPerThread; ++j) {
+  for (int j = 0; j < kFinePer; ++j) {
     if (slot[j] == kReject) continue;
     const unsigned pos = start[(slot[j] >> kWinShift) & (kFinePerCoarse - 1)] + rank[j];
     t_slot[pos] = slot[j];
@@ -554,7 +568,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_fine(Stage A, const unsigne
   }
   __syncthreads();
   unsigned err = 0;
-  for (unsigned p = t; p < total; p += kBinThreads) {
+  for (unsigned p = t; p < total; p += kFineThreads) {
     const unsigned sl = t_slot[p];
     const unsigned f = (sl >> kWinShift) & (kFinePerCoarse - 1);
     const unsigned r = gbase[f] + (p - start[f]);
@@ -1097,16 +1111,15 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     for (int j = 0; j < CPT; ++j) {
       long long idx = half_base + ((excl >> (16 * j)) & 0xFFFFu);
       half_base += (wsum[NW] >> (16 * j)) & 0xFFFFu;
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        if (!((emit[j] >> d) & 1u)) continue;
-        const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+      for (unsigned todo = emit[j]; todo; todo &= todo - 1u) {   // the emitted duals only
+        const int d = __ffs(todo) - 1;
+        const int rd = c0[j] + (d & 1) + RS * ((d >> 1) & 1) + PS * (d >> 2);
         unsigned v[8];
         unsigned all_same = kSame;
         int cas = 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int r = c0[j] + (dx + (e & 1)) + RS * (dy + ((e >> 1) & 1)) + PS * (dz + (e >> 2));
+          const int r = rd + (e & 1) + RS * ((e >> 1) & 1) + PS * (e >> 2);
           all_same &= rv[r];
           v[e] = rv[r] & ~kSame;
           if (ISO) cas |= (rsc[r] > iso ? 1 : 0) << e;
@@ -1506,8 +1519,8 @@ BinLayout bin_layout(long long n_slots) {
 }
 
 namespace {
-constexpr int kSmemCoarse = (2 * kMaxCoarse + 3 * kBinTile) * 4;
-constexpr int kSmemFine = (2 * kFinePerCoarse + 3 * kBinTile) * 4;
+constexpr int kSmemCoarse = (2 * kMaxCoarse + 3 * kCoarseTile) * 4;
+constexpr int kSmemFine = (2 * kFinePerCoarse + 3 * kFineTile) * 4;
 constexpr int kSmemPlace = kWinSlots * 8;
 
 struct Stages {
@@ -1549,19 +1562,20 @@ cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl
       (e = cudaFuncSetAttribute(k_place_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)))
     return e;
   if (n <= 0) return cudaSuccess;
-  const long long tiles = (n + kBinTile - 1) / kBinTile;
+  const long long tiles = (n + kCoarseTile - 1) / kCoarseTile;
+  const int smem_coarse = (2 * (int)lay.n_coarse + 3 * kCoarseTile) * 4;   // kSmemCoarse at most
   AMR_DISPATCH(logb, ({
     int per_sm = 0;   // one resident wave: the tile loop is grid-strided
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, codes ? k_bin_coarse<LB, true> : k_bin_coarse<LB, false>, kBinThreads, kSmemCoarse)) !=
+             &per_sm, codes ? k_bin_coarse<LB, true> : k_bin_coarse<LB, false>, kCoarseThreads, smem_coarse)) !=
         cudaSuccess)
       return e;
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count * std::max(per_sm, 1));
     if (codes)
-      k_bin_coarse<LB, true><<<grid, kBinThreads, kSmemCoarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse, S.a,
+      k_bin_coarse<LB, true><<<grid, kCoarseThreads, smem_coarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse, S.a,
                                                                      S.coarse_count, sc, codes);
     else
-      k_bin_coarse<LB, false><<<grid, kBinThreads, kSmemCoarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse,
+      k_bin_coarse<LB, false><<<grid, kCoarseThreads, smem_coarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse,
                                                                       S.a, S.coarse_count, sc, nullptr);
   }));
   return cudaGetLastError();
@@ -1571,7 +1585,7 @@ cudaError_t launch_bin_fine(long long n_slots, void* staging, Scratch* sc, cudaS
   const BinLayout lay = bin_layout(n_slots);
   if (n_slots <= 0) return cudaSuccess;
   const Stages S = stages_of(lay, staging);
-  k_bin_fine<<<dim3((1u << kCoarseShift) / kBinTile, (unsigned)lay.n_coarse), kBinThreads, kSmemFine, st>>>(
+  k_bin_fine<<<dim3((1u << kCoarseShift) / kFineTile, (unsigned)lay.n_coarse), kFineThreads, kSmemFine, st>>>(
       S.a, S.coarse_count, S.b, S.win_count, sc);
   return cudaGetLastError();
 }
