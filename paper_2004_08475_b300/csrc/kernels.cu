@@ -1229,10 +1229,11 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
 }
 
 // Dynamic shared memory of k_mc<·, EMIT> per CTA of 256 threads: per warp
-// 64 rows (two duals per lane) of 8 vertex slots and 8 scalars, a list of
-// the step's kept triangles and their staged vertices.
+// 64 rows (two duals per lane) of 8 vertex slots, a list of the step's kept
+// triangles and their staged vertices (46 KB with the static table: four
+// CTAs per SM).
 constexpr int kMcRowsWords = 8 * 64 * kRow;
-constexpr int kMcSmemBytes = 4 * (2 * kMcRowsWords + 8 * kTriStage + 8 * kTriStage * 9);
+constexpr int kMcSmemBytes = 4 * (kMcRowsWords + 8 * kTriStage + 8 * kTriStage * 9);
 
 // One lane per dual, two duals per lane per step: gather the 8 vertex
 // scalars, build the case index (bit e set iff s_e > iso), keep the case's
@@ -1243,7 +1244,7 @@ constexpr int kMcSmemBytes = 4 * (2 * kMcRowsWords + 8 * kTriStage + 8 * kTriSta
 // them, and write the step's triangles as one coalesced run. Optionally
 // writes per-dual case and triangle count instead.
 template <int LOGB, bool EMIT, bool CASES>
-__global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
+__global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
                                             float iso, float* __restrict__ tris, long long cap,
                                             unsigned long long* counter, unsigned char* cases,
                                             unsigned char* ntri, const __grid_constant__ McConst mc) {
@@ -1255,9 +1256,8 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + w;
   unsigned* rows_v = mc_smem + w * 64 * kRow;                               // [64][kRow]
-  float* rows_s = reinterpret_cast<float*>(mc_smem + kMcRowsWords) + w * 64 * kRow;
-  unsigned* list = mc_smem + 2 * kMcRowsWords + w * kTriStage;             // [kTriStage]
-  float* wst = reinterpret_cast<float*>(mc_smem + 2 * kMcRowsWords + 8 * kTriStage) + w * kTriStage * 9;
+  unsigned* list = mc_smem + kMcRowsWords + w * kTriStage;                 // [kTriStage]
+  float* wst = reinterpret_cast<float*>(mc_smem + kMcRowsWords + 8 * kTriStage) + w * kTriStage * 9;
   for (long long base = wid * 64; base < nd; base += nwarps * 64) {
     const long long d0 = base + lane, d1 = base + 32 + lane;
     const bool a0 = d0 < nd, a1 = d1 < nd;
@@ -1288,9 +1288,14 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
       const unsigned total = __reduce_add_sync(kFull, mine);
       long long idx = warp_append(mine, counter);
       unsigned* r0 = rows_v + lane * kRow;   // rows lane and 32 + lane: conflict-free
-      float* q0 = rows_s + lane * kRow;
-      if (k0) stage_row(r0, q0, v0, s0);
-      if (k1) stage_row(r0 + 32 * kRow, q0 + 32 * kRow, v1, s1);
+      if (k0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r0[e] = v0[e];
+      }
+      if (k1) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r0[32 * kRow + e] = v1[e];
+      }
       if (total <= (unsigned)kTriStage) {
         const long long first = __shfl_sync(kFull, idx, 0);
         unsigned pos = (unsigned)(idx - first);
@@ -1304,11 +1309,11 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
           const unsigned e = q / 3u, c = q - 3u * e;
           const unsigned ent = list[e];
           const unsigned* rv = rows_v + (ent & 0xFFu) * kRow;
-          const float* rs = rows_s + (ent & 0xFFu) * kRow;
           const int k = (int)((ent >> (8 + 4 * c)) & 15u);
           const int a = (int)((mc.edge_a >> (4 * k)) & 15), b = (int)((mc.edge_b >> (4 * k)) & 15);
-          const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, rv[a]), rs[a], slot_cell<LOGB>(L.bricks, rv[b]),
-                                       rs[b], iso);
+          const unsigned va = rv[a], vb = rv[b];   // scalars gathered again: just read, so cached
+          const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, va), __ldg(L.scal + va),
+                                       slot_cell<LOGB>(L.bricks, vb), __ldg(L.scal + vb), iso);
           wst[3 * q] = p.x;
           wst[3 * q + 1] = p.y;
           wst[3 * q + 2] = p.z;
@@ -1317,14 +1322,20 @@ __global__ void __launch_bounds__(256) k_mc(Locator L, const uint4* __restrict__
         const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
         for (long long k = lane; k < lim; k += 32) tris[9 * first + k] = wst[k];
         __syncwarp();
-      } else {   // more triangles than the stage holds: each lane writes its own
+      } else {   // more triangles than the stage holds: each lane writes its own (scalars in the stage)
+        float* q0 = wst + lane * 2 * kRow;
         if (k0) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) q0[e] = s0[e];
           write_triangles<LOGB>(L.bricks, r0, q0, iso, sh.packed[c0], k0, idx, cap, tris, mc.edge_a, mc.edge_b);
           idx += __popc(k0);
         }
-        if (k1)
-          write_triangles<LOGB>(L.bricks, r0 + 32 * kRow, q0 + 32 * kRow, iso, sh.packed[c1], k1, idx, cap, tris,
+        if (k1) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) q0[kRow + e] = s1[e];
+          write_triangles<LOGB>(L.bricks, r0 + 32 * kRow, q0 + kRow, iso, sh.packed[c1], k1, idx, cap, tris,
                                 mc.edge_a, mc.edge_b);
+        }
         __syncwarp();
       }
     }
