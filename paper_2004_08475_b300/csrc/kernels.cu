@@ -1388,7 +1388,9 @@ __global__ void __launch_bounds__(256) k_mc_batch_count(Locator L, const uint4* 
 // Batched iso-values, emit pass: a persistent grid pulls tiles of dual cells
 // from a device counter (no waiting on other CTAs); every dual's vertices and
 // scalars are read once and tested against all iso-values; iso k's triangles
-// go to its own segment tris[seg_off[k] ...] through counter n_tri[k].
+// go to its own segment tris[seg_off[k] ...] through counter n_tri[k]. Per
+// iso-value the warp lists its kept triangles and computes their vertices
+// lane-parallel into a stage written as one coalesced run, as in k_mc.
 template <int LOGB>
 __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* __restrict__ duals,
                                                        long long nd, const float* __restrict__ isos,
@@ -1400,10 +1402,13 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
   __shared__ float iso_sh[kMaxIso];
   __shared__ long long off_sh[kMaxIso + 1];
   __shared__ long long tile_base;
-  __shared__ unsigned row_v[256 * kRow];
-  __shared__ float row_s[256 * kRow];
-  unsigned* vr = row_v + threadIdx.x * kRow;
-  float* sr = row_s + threadIdx.x * kRow;
+  __shared__ unsigned rows[256 * kRow];                     // each lane's dual: 8 vertex slots
+  __shared__ unsigned tlist[8][kTriStage];
+  __shared__ __align__(16) float tstage[8][kTriStage * 9];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned* myrow = rows + threadIdx.x * kRow;
+  unsigned* lst = tlist[w];
+  float* wst = tstage[w];
   load_mc(sh, mc);
   for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
     iso_sh[k] = isos[k];
@@ -1419,7 +1424,7 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
     if (t0 >= nd) break;
     const long long t1 = min(nd, t0 + tile);
     for (long long base = t0 + (threadIdx.x & ~31); base < t1; base += blockDim.x) {
-      const long long d = base + (threadIdx.x & 31);
+      const long long d = base + lane;
       unsigned v[8];
       float sv[8];
       float mn = 3.4e38f, mx = -3.4e38f;
@@ -1432,8 +1437,10 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
           sv[e] = __ldg(L.scal + v[e]);
           mn = fminf(mn, sv[e]);
           mx = fmaxf(mx, sv[e]);
+          myrow[e] = v[e];
         }
       }
+      __syncwarp();
       for (int k = 0; k < n_iso; ++k) {
         const float iso = iso_sh[k];
         unsigned keep = 0;
@@ -1444,15 +1451,44 @@ __global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* _
           keep = kept_of(distinct, sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
         }
         if (__ballot_sync(kFull, keep != 0) == 0) continue;
-        const long long idx = warp_append(__popc(keep), &sc->n_tri[k]);
-        if (keep) {
-          // rows of segment k that fit the buffer (all of them unless the
-          // caller's capacity was short)
-          const long long cap = max(0ll, min(off_sh[k + 1], total_cap) - off_sh[k]);
-          stage_row(vr, sr, v, sv);
-          write_triangles<LOGB>(L.bricks, vr, sr, iso, sh.packed[cas], keep, idx, cap, tris + 9 * off_sh[k],
-                                mc.edge_a, mc.edge_b);
+        const unsigned mine = __popc(keep);
+        const unsigned total = __reduce_add_sync(kFull, mine);
+        long long idx = warp_append(mine, &sc->n_tri[k]);
+        // rows of segment k that fit the buffer (all of them unless the
+        // caller's capacity was short)
+        const long long cap = max(0ll, min(off_sh[k + 1], total_cap) - off_sh[k]);
+        float* segk = tris + 9 * off_sh[k];
+        if (total <= (unsigned)kTriStage) {
+          const long long first = __shfl_sync(kFull, idx, 0);
+          unsigned pos = (unsigned)(idx - first);
+          const unsigned long long pk = sh.packed[cas];
+          for (int t = 0; t < 5; ++t)
+            if ((keep >> t) & 1u) lst[pos++] = (unsigned)lane | ((unsigned)(pk >> (12 * t)) & 0xFFFu) << 8;
+          __syncwarp();
+          for (unsigned q = lane; q < 3u * total; q += 32) {   // one vertex per lane
+            const unsigned e = q / 3u, c = q - 3u * e;
+            const unsigned ent = lst[e];
+            const unsigned* rv = rows + (w * 32 + (ent & 31u)) * kRow;
+            const int kk = (int)((ent >> (8 + 4 * c)) & 15u);
+            const int a = (int)((mc.edge_a >> (4 * kk)) & 15), b = (int)((mc.edge_b >> (4 * kk)) & 15);
+            const unsigned va = rv[a], vb = rv[b];
+            const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, va), __ldg(L.scal + va),
+                                         slot_cell<LOGB>(L.bricks, vb), __ldg(L.scal + vb), iso);
+            wst[3 * q] = p.x;
+            wst[3 * q + 1] = p.y;
+            wst[3 * q + 2] = p.z;
+          }
+          __syncwarp();
+          const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
+          for (long long kk = lane; kk < lim; kk += 32) segk[9 * first + kk] = wst[kk];
+        } else if (keep) {   // more triangles than the stage holds: each lane writes its own
+          float* q0 = wst + lane * kRow;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) q0[e] = sv[e];
+          write_triangles<LOGB>(L.bricks, myrow, q0, iso, sh.packed[cas], keep, idx, cap, segk, mc.edge_a,
+                                mc.edge_b);
         }
+        __syncwarp();
       }
     }
   }
