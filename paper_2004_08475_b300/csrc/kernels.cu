@@ -1013,11 +1013,13 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     const int4 b = __ldg(L.bricks + bi);
     const int l = b.w;
     bool mine[CPT];
+    bool level_only = true;   // every region entry this thread loads is a cell of level l
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {   // the brick itself: coalesced reads
       const unsigned s2 = ((unsigned)bi << (3 * LOGB)) | (unsigned)(t + j * NT);
       const unsigned v = __ldg(L.view + s2);
       mine[j] = v == s2;
+      level_only = level_only && mine[j];
       const int r = c0[j] + 1 + RS + PS;
       rv[r] = mine[j] ? (v | kSame) : v;
       if (v != kReject)
@@ -1045,8 +1047,11 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
       }
       rv[rx + RS * ry + PS * rz] = same ? (v | kSame) : v;
       if (v != kReject) atomicOr(&rmask[ry + R * rz], (1u << rx) | ((same ? 1u : 0u) << (16 + rx)));
+      level_only = level_only && same;
     }
-    __syncthreads();
+    // A region made only of level-l cells leaves each cell exactly one dual:
+    // the one it is the lowest vertex of (d = 7); rules 1-3 need not run.
+    const bool uniform = __syncthreads_and(level_only) != 0;
     if (ISO) {
       for (int q = t; q < NR; q += NT) {
         const int r = q % R + RS * ((q / R) % R) + PS * (q / (R * R));
@@ -1061,6 +1066,11 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     for (int j = 0; j < CPT; ++j) {
       emit[j] = 0;
       if (!mine[j]) continue;   // the slot holds no level-l cell
+      if (uniform) {
+        emit[j] = 0x80u;
+        cnt += 1u << (16 * j);
+        continue;
+      }
       unsigned exist = 0, samem = 0;
 #pragma unroll
       for (int oz = 0; oz < 3; ++oz)
