@@ -17,6 +17,7 @@ added to the same line.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -57,14 +58,14 @@ WORKLOADS = {
 
 def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int, placement: int = 0) -> float:
     """Compulsory bytes per launch of each kernel under the library's data
-    layout: what the kernel must read and write at least once. placement 2:
-    the insert pass records each cell's 4-byte table code and the coarse
-    binning reads it instead of the cell's corner and level."""
-    coded = placement == 2
+    layout: what the kernel must read and write at least once. placement 1
+    (binned): the insert pass records each cell's 4-byte table code and the
+    coarse binning reads it instead of the cell's corner and level."""
+    coded = placement == 1
     return {
         "k_insert_bricks": 13.0 * n + (4.0 * n if coded else 0.0),   # xyz + level (+ code)
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
-        "k_bin_coarse": (8.0 if coded else 17.0) * n + 12.0 * n,   # read the cell, write a 12-byte entry
+        "k_bin_coarse": 8.0 * n + 12.0 * n,          # read code + scalar, write a 12-byte entry
         "k_bin_fine": 12.0 * n + 12.0 * n,           # re-split the entries by window
         "k_place_windows": 12.0 * n + 8.0 * n_slots, # read the entries, write every slot's record
         "k_resolve_views": 16.0 * n_slots,           # read the record, write view + scalar
@@ -353,6 +354,7 @@ def main():
                     help="amr_dual_cells_iso (one pass) instead of amr_dual_cells then amr_iso")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-indexed", action="store_true", help="skip the indexed face set measurement")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--batch-isos", type=int, default=16)
     ap.add_argument("--mode", default="step", choices=["step", "serve"])
@@ -491,6 +493,56 @@ def main():
         del buf
         torch.cuda.empty_cache()
 
+    # indexed face set of the step's iso-value (vertices welded by edge key)
+    indexed = None
+    if not args.no_indexed and rank == 0:
+        vtx, tri, _ = ctx.iso_indexed(iso, with_keys=False)   # sizes the library's and our buffers
+        nv, ntr = int(vtx.shape[0]), int(tri.shape[0])
+        torch.cuda.synchronize()
+        ctx.kernel_times()
+        ctx.enable_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        vb = torch.empty((nv, 3), dtype=torch.float32, device="cuda")
+        tb = torch.empty((ntr, 3), dtype=torch.int32, device="cuda")
+        cnv, cnt_ = ctypes.c_int64(0), ctypes.c_int64(0)
+        e0.record(stream)
+        for _ in range(reps):
+            rc = amriso.lib().amr_iso_indexed(ctx._h, ctypes.c_float(iso), vb.data_ptr(), nv, tb.data_ptr(), ntr,
+                                              None, ctypes.byref(cnv), ctypes.byref(cnt_), amriso.DEVICE_PTRS)
+            assert rc == 0 and cnv.value == nv and cnt_.value == ntr
+        e1.record(stream)
+        torch.cuda.synchronize()
+        it = ctx.kernel_times()
+        ctx.enable_timing(False)
+        ims = e0.elapsed_time(e1) / reps
+        indexed = {"ms": ims, "vertices": nv, "triangles": ntr, "triangles_per_s": ntr / (ims / 1e3),
+                   "bytes_fat": 36 * ntr, "bytes_indexed": 12 * nv + 12 * ntr,
+                   "kernels_ms": {k: v[0] / reps for k, v in it.items() if v[1]}}
+        del vtx, tri, vb, tb
+        # a second per-cell field at those vertices (here the scalar itself)
+        _, _, vkeys = ctx.iso_indexed(iso, with_keys=True)
+        ctx.interpolate(iso, s, vkeys)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.interpolate(iso, s, vkeys)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        indexed["interpolate_ms"] = e0.elapsed_time(e1) / reps
+        del vkeys
+        # shapes of the dual cells (distinct cells among the 8 vertices)
+        _, hist = ctx.dual_shapes()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.dual_shapes()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        indexed["dual_shapes"] = {"ms": e0.elapsed_time(e1) / reps,
+                                  "histogram_by_distinct_cells": [int(v) for v in hist]}
+        torch.cuda.empty_cache()
+
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -546,7 +598,7 @@ def main():
             "config": {"workload": args.workload, "description": desc, "n_cells": n,
                        "step": "fused" if args.fused_iso else "dual_cells+iso",
                        "n_dual": nd, "n_triangles": nt, "iso": iso, "n_bricks": inf.n_bricks,
-                       "placement": ["direct", "binned", "binned+codes"][inf.placement],
+                       "placement": ["direct", "binned"][inf.placement],
                        "n_slots": inf.n_slots, "levels": inf.n_levels, "log2_brick": args.log2_brick,
                        "load_factor": args.load_factor, "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 ({(17 * n) / 1e6:.0f} MB of cells)"},
@@ -558,6 +610,7 @@ def main():
             "roofline": roofline,
             "kernels": kernels,
             "batched_iso": batch,
+            "indexed_face_set": indexed,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),

@@ -64,7 +64,10 @@ typedef struct amr_locator_opts {
   int   partitioned;    /* cell placement: > 0 always binned (a two-level
                            split by slot, then each window of slots built in
                            shared memory and written whole), < 0 always a
-                           direct scatter, 0 binned from 2^20 cells on  [0] */
+                           direct scatter, 0 binned from 2^20 cells on; the
+                           binned form needs a brick table of at most
+                           2^(32 - 3 log2_brick) entries and otherwise falls
+                           back to the direct scatter                   [0] */
 } amr_locator_opts;
 
 /* ---- context ------------------------------------------------------------ */
@@ -89,7 +92,8 @@ int amr_set_stream(amr_ctx* ctx, void* cuda_stream);
  *   scalar [n]    fp32 cell-centred values
  * With AMR_HOST_PTRS the arrays are copied to the device inside the call.
  * With device pointers the arrays are borrowed: they must stay valid and
- * unchanged until amr_build_locator returns (AMR_COPY copies them instead).
+ * unchanged until amr_build_locator returns, and xyz and scalar as long as
+ * amr_interpolate is called on the context (AMR_COPY copies them instead).
  * Validation (alignment, level range, finiteness) happens in
  * amr_build_locator. Invalidates any locator / dual cells of the context. */
 int amr_upload(amr_ctx* ctx, const int32_t* xyz, const uint8_t* level,
@@ -144,6 +148,49 @@ int amr_get_duals(amr_ctx* ctx, int32_t* out, int64_t cap, int flags);
 int amr_iso(amr_ctx* ctx, float iso, float* tris, int64_t cap, int64_t* n_tris,
             int flags);
 
+/* Indexed face set of the same surface (the indexed output the paper builds
+ * after its extraction, Sec. 5.2, with vertices welded by their integer edge
+ * key - the unordered pair of cells a vertex interpolates between - instead
+ * of by sorting positions): the triangles of amr_iso, each as three vertex
+ * indices in the same orientation; every edge key once as a vertex, at the
+ * same fp32 position amr_iso computes for it.
+ *   vtx   [vcap][3] fp32 vertex positions (unspecified order);
+ *   tri   [tcap][3] int32 vertex indices;
+ *   vkeys [vcap][2] int32 (may be NULL): each vertex's two cells as input
+ *         indices, smaller first.
+ *   *n_vtx, *n_tri receive the exact counts; when either exceeds its
+ *   capacity the call returns AMR_ERR_CAPACITY and only the first vcap
+ *   vertices / tcap triangles were written (a triangle may then refer to an
+ *   unwritten vertex). flags: AMR_DEVICE_PTRS or AMR_HOST_PTRS for all three
+ *   arrays. Synchronises the stream. */
+int amr_iso_indexed(amr_ctx* ctx, float iso, float* vtx, int64_t vcap, int32_t* tri, int64_t tcap,
+                    int32_t* vkeys, int64_t* n_vtx, int64_t* n_tri, int flags);
+
+/* A second per-cell field interpolated at the vertices of an indexed face
+ * set, along the same edges and with the same t as their positions (the
+ * attribute mapping of the paper's introduction, Sec. 1): for vertex v with
+ * cells (a, b) = vkeys[v] (input indices, as amr_iso_indexed returns them),
+ * taken from the one with the lower (z,y,x) corner, t = (iso - s_a) /
+ * (s_b - s_a) and out[v] = f_a + t (f_b - f_a), each fp32 operation rounded
+ * on its own. iso must be the value the face set was extracted at.
+ *   attr [n_cells] fp32 per input cell; vkeys [nv][2]; out [nv].
+ * flags: AMR_DEVICE_PTRS or AMR_HOST_PTRS for all three arrays. A cell index
+ * outside [0, n_cells) gives AMR_ERR_RANGE (and 0 for that vertex). Reads
+ * the corners and scalars given to amr_upload (borrowed device arrays must
+ * still be valid). Synchronises the stream. */
+int amr_interpolate(amr_ctx* ctx, float iso, const float* attr, const int32_t* vkeys, int64_t nv, float* out,
+                    int flags);
+
+/* Shapes of the resident dual cells: snapping collapses a dual hexahedron
+ * to a wedge, pyramid, tetrahedron or a flatter shape when several of its 8
+ * vertices resolve to the same cell (Sec. 4.1, Sec. 5). counts[d] (may be
+ * NULL) receives the number of distinct cells among dual d's vertices
+ * (8 hexahedron, 6 wedge, 5 pyramid, 4 tetrahedron), in the dual list's
+ * order (as amr_get_duals); hist[0..8] (may be NULL, host memory) the number
+ * of duals with each count. flags (AMR_DEVICE_PTRS / AMR_HOST_PTRS) apply to
+ * counts. Synchronises the stream. */
+int amr_dual_shapes(amr_ctx* ctx, uint8_t* counts, int64_t* hist, int flags);
+
 /* Per-dual MC case index and number of kept triangles at `iso`, in the order
  * of amr_get_duals: cases[n_dual] uint8, ntri[n_dual] uint8 (either may be
  * NULL). Synchronises the stream. */
@@ -193,7 +240,7 @@ const char* amr_strerror(int code);
  * of the build); a binding compares it with the header it was written for
  * and refuses a library built from other sources. No counterpart in the
  * paper. */
-#define AMR_ABI_VERSION 4
+#define AMR_ABI_VERSION 8
 int amr_abi_version(void);
 
 /* ---- introspection (host only, no device needed) ------------------------ */
@@ -216,8 +263,7 @@ typedef struct amr_info {
   int32_t log2_brick;
   int64_t device_bytes; /* device memory held by the context */
   int32_t placement;    /* how the last amr_build_locator placed the cells:
-                           0 direct scatter, 1 binned, 2 binned with each
-                           cell's table entry recorded by the insert pass */
+                           0 direct scatter, 1 binned */
   int32_t reserved;
 } amr_info;
 int amr_get_info(amr_ctx* ctx, amr_info* info);

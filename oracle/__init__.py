@@ -11,6 +11,12 @@ Functions follow the paper's steps:
   * ``.duals()``        - doCell / doDualCell with rules 1-3 (Sec. 4.2-4.4)
   * ``.iso()``          - Marching Cubes on the dual hexahedra (Sec. 5, 5.2)
   * ``case_triangles``  - the run-time face walk for one MC case (Sec. 5.1)
+  * ``weld``            - the indexed face set of a triangle list (Sec. 5.2),
+                          vertices identified by their edge key
+  * ``interpolate``     - a second per-cell field at those vertices (the
+                          attribute mapping of Sec. 1)
+  * ``dual_shapes``     - distinct cells per dual (the shapes snapping
+                          produces, Sec. 4.1)
 
 Pins (tests/test_oracle_*.py): brute-force snapping of every logical dual on
 tiny inputs, the (n-1)^3 closed form on uniform grids, the sphere's Euler
@@ -142,6 +148,53 @@ class OracleMesh:
         assert nt2 == nt
         return {"cases": cases, "ntri": ntri, "tris": tris, "keys": keys,
                 "tri_dual": tdual, "max_err": err.value}
+
+
+def weld(tris, keys):
+    """Indexed face set of fat triangles (Sec. 5.2). The paper merges
+    vertices at equal positions after sorting; here a vertex is identified by
+    its edge key (the unordered pair of cells it interpolates between), so
+    each distinct key becomes one vertex.
+
+    tris [T,3,3] f32 and keys [T,3,2] (from ``OracleMesh.iso``) -> (vtx [V,3]
+    f32, tri [T,3] i64, vkeys [V,2] i64), vertices in increasing key order.
+    Raises if one key carries two different positions."""
+    k = np.asarray(keys, dtype=np.int64).reshape(-1, 2)
+    p = np.asarray(tris, dtype=np.float32).reshape(-1, 3)
+    if k.shape[0] == 0:
+        return (np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int64), np.zeros((0, 2), np.int64))
+    vkeys, first, inv = np.unique(k, axis=0, return_index=True, return_inverse=True)
+    vtx = p[first]
+    if not np.array_equal(vtx[inv.reshape(-1)].view(np.int32), p.view(np.int32)):
+        raise OracleError("one edge key with two vertex positions")
+    return vtx, inv.reshape(-1, 3).astype(np.int64), vkeys
+
+
+def interpolate(xyz, scalar, attr, vkeys, iso):
+    """A per-cell field at the vertices of an indexed face set: for a vertex
+    on the edge of cells (a, b), taken from the one whose lower corner is
+    lower in (z, y, x) order, t = (iso - s_a) / (s_b - s_a) and
+    f = f_a + t (f_b - f_a), every step in fp32 (the vertex formula of
+    Sec. 5 applied to another field)."""
+    x = np.asarray(xyz, dtype=np.int64).reshape(-1, 3)
+    s = np.asarray(scalar, dtype=np.float32).reshape(-1)
+    f = np.asarray(attr, dtype=np.float32).reshape(-1)
+    k = np.asarray(vkeys, dtype=np.int64).reshape(-1, 2)
+    a, b = k[:, 0].copy(), k[:, 1].copy()
+    za, zb = x[a][:, ::-1], x[b][:, ::-1]   # (z, y, x)
+    swap = np.array([tuple(q) < tuple(p) for p, q in zip(za.tolist(), zb.tolist())], dtype=bool)
+    a[swap], b[swap] = k[swap, 1], k[swap, 0]
+    iso32 = np.float32(iso)
+    t = (iso32 - s[a]) / (s[b] - s[a])
+    return (f[a] + t * (f[b] - f[a])).astype(np.float32)
+
+
+def dual_shapes(duals) -> np.ndarray:
+    """Number of distinct cells among each dual's 8 vertices (Sec. 4.1:
+    snapping makes hexahedra, wedges, pyramids, tetrahedra and flatter
+    shapes): 8, 6, 5, 4, ..."""
+    d = np.sort(np.asarray(duals, dtype=np.int64).reshape(-1, 8), axis=1)
+    return (1 + (d[:, 1:] != d[:, :-1]).sum(axis=1)).astype(np.uint8)
 
 
 def case_triangles(case: int) -> np.ndarray:

@@ -62,7 +62,7 @@ class _Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("placement", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-ABI_VERSION = 4   # AMR_ABI_VERSION of include/amriso.h
+ABI_VERSION = 8   # AMR_ABI_VERSION of include/amriso.h
 
 
 def _load() -> ctypes.CDLL:
@@ -81,6 +81,9 @@ def _load() -> ctypes.CDLL:
         "amr_get_duals": (I, [P, P, I64, I]),
         "amr_dual_cells_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), I]),
         "amr_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), I]),
+        "amr_iso_indexed": (I, [P, F, P, I64, P, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64), I]),
+        "amr_interpolate": (I, [P, F, P, P, I64, P, I]),
+        "amr_dual_shapes": (I, [P, P, P, I]),
         "amr_iso_cases": (I, [P, F, P, P, I]),
         "amr_iso_batch": (I, [P, P, I, P, I64, P, I]),
         "amr_iso_batch_async": (I, [P, P, I, P, I64, P]),
@@ -112,7 +115,8 @@ EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_bui
            "amr_dual_cells", "amr_get_duals", "amr_iso", "amr_iso_cases", "amr_iso_batch",
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
            "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async",
-           "amr_dual_cells_iso", "amr_trim", "amr_abi_version")
+           "amr_dual_cells_iso", "amr_trim", "amr_abi_version", "amr_iso_indexed",
+           "amr_interpolate", "amr_dual_shapes")
 
 
 def lib() -> ctypes.CDLL:
@@ -153,7 +157,7 @@ class Info:
     n_levels: int
     log2_brick: int
     device_bytes: int
-    placement: int = 0   # 0 direct scatter, 1 binned, 2 binned with insert-pass codes
+    placement: int = 0   # 0 direct scatter, 1 binned
 
 
 class AmrContext:
@@ -175,6 +179,7 @@ class AmrContext:
         if getattr(self, "_h", None):
             _lib.amr_destroy(self._h)
             self._h = None
+        self._keep = None
 
     def __del__(self):
         try:
@@ -189,8 +194,9 @@ class AmrContext:
     # -- hot path ----------------------------------------------------------
     def upload(self, xyz, level, scalar, copy: bool = False):
         """xyz int32 [N,3], level uint8 [N], scalar fp32 [N]; all on the GPU
-        (borrowed until build_locator returns, unless copy=True) or all on
-        the host (copied inside the call)."""
+        (borrowed: this object keeps them alive until the next upload or
+        close, since interpolate reads xyz and scalar; copy=True copies) or
+        all on the host (copied inside the call)."""
         xyz = xyz.contiguous()
         level = level.contiguous()
         scalar = scalar.contiguous()
@@ -209,11 +215,11 @@ class AmrContext:
                       check_overlap: bool = False, partitioned: int = 0):
         """partitioned: 1 places the cells by the binned passes (split by
         slot range, then each window of slots written whole), -1 by a direct
-        scatter, 0 binned from 2^20 cells on."""
+        scatter, 0 binned from 2^20 cells on (binned falls back to the direct
+        scatter when the brick table outgrows the cell codes)."""
         o = _LocatorOpts(int(log2_brick), float(load_factor), int(block_size), int(check_overlap),
                          int(partitioned))
         rc = _lib.amr_build_locator(self._h, ctypes.byref(o))
-        self._keep = None
         _check(rc, "amr_build_locator")
 
     def dual_cells(self) -> int:
@@ -260,6 +266,54 @@ class AmrContext:
                               ctypes.byref(n), flags)
         _check(rc, "amr_iso")
         return out[:n.value]
+
+    def iso_indexed(self, iso: float, host: bool = False, with_keys: bool = True):
+        """Indexed face set at `iso`: (vtx [V,3] f32, tri [T,3] i32, keys [V,2]
+        i32 input-cell indices or None), on the device or in host memory."""
+        nv, nt = ctypes.c_int64(0), ctypes.c_int64(0)
+        flags = HOST_PTRS if host else DEVICE_PTRS
+        dev = "cpu" if host else self.device
+        vcap = max(1024, self.n_dual // 4)
+        tcap = vcap
+        for _ in range(2):
+            vtx = torch.empty((vcap, 3), dtype=torch.float32, device=dev)
+            tri = torch.empty((tcap, 3), dtype=torch.int32, device=dev)
+            keys = torch.empty((vcap, 2), dtype=torch.int32, device=dev) if with_keys else None
+            if host:
+                vtx, tri = vtx.pin_memory(), tri.pin_memory()
+                keys = keys.pin_memory() if keys is not None else None
+            rc = _lib.amr_iso_indexed(self._h, ctypes.c_float(iso), _ptr(vtx), vcap, _ptr(tri), tcap,
+                                      _ptr(keys) if keys is not None else None, ctypes.byref(nv),
+                                      ctypes.byref(nt), flags)
+            if rc != ERR_CAPACITY:
+                break
+            vcap, tcap = max(vcap, nv.value), max(tcap, nt.value)
+        _check(rc, "amr_iso_indexed")
+        return vtx[:nv.value], tri[:nt.value], (keys[:nv.value] if keys is not None else None)
+
+    def interpolate(self, iso: float, attr: torch.Tensor, vkeys: torch.Tensor) -> torch.Tensor:
+        """Per-vertex values of the per-cell field `attr` [n] f32 at the
+        vertices `vkeys` [V,2] (from iso_indexed) of the surface at `iso`;
+        on the device of `attr`."""
+        host = not attr.is_cuda
+        attr = attr.contiguous().to(torch.float32)
+        vkeys = vkeys.contiguous().to(torch.int32)
+        if host:
+            attr, vkeys = attr.pin_memory(), vkeys.pin_memory()
+        out = torch.empty(vkeys.shape[0], dtype=torch.float32, device=attr.device)
+        if host:
+            out = out.pin_memory()
+        _check(_lib.amr_interpolate(self._h, ctypes.c_float(iso), _ptr(attr), _ptr(vkeys), int(vkeys.shape[0]),
+                                    _ptr(out), HOST_PTRS if host else DEVICE_PTRS), "amr_interpolate")
+        return out
+
+    def dual_shapes(self):
+        """Per resident dual the number of distinct cells among its 8
+        vertices (u8 [n_dual] on the device) and the histogram over 0..8."""
+        counts = torch.empty(max(self.n_dual, 0), dtype=torch.uint8, device=self.device)
+        hist = np.zeros(9, dtype=np.int64)
+        _check(_lib.amr_dual_shapes(self._h, _ptr(counts), hist.ctypes.data, DEVICE_PTRS), "amr_dual_shapes")
+        return counts, hist
 
     def iso_count(self, iso: float, out: torch.Tensor) -> int:
         """amr_iso into a preallocated buffer; returns the exact count (may

@@ -9,7 +9,9 @@
 #include <vector>
 
 #include "amriso.h"
+#include "attributes.h"
 #include "kernels.h"
+#include "shapes.h"
 #include "mc_table.h"
 
 using namespace amriso;
@@ -27,12 +29,14 @@ struct DevBuf {
 
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
-  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_BIN_FINE, KT_COUNT
+  KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_BIN_FINE, KT_MC_KEYS, KT_WELD_INSERT,
+  KT_WELD_INDEX, KT_INTERPOLATE, KT_SHAPES, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
     "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
-    "k_bin_coarse", "k_place_windows", "k_dual_cells_iso", "k_bin_fine"};
+    "k_bin_coarse", "k_place_windows", "k_dual_cells_iso", "k_bin_fine", "k_mc_keys", "k_weld_insert",
+    "k_weld_index", "k_interpolate", "k_dual_shapes"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -78,7 +82,7 @@ struct amr_ctx {
   int block = 256;
   int check_overlap = 0;
   DevBuf htab, bricks, rec, scal, view, nbr, staging, codes;
-  int placement = 0;   // 0 direct scatter, 1 binned, 2 binned with insert-pass codes
+  int placement = 0;   // 0 direct scatter, 1 binned
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
   int levels = 0;
@@ -89,6 +93,8 @@ struct amr_ctx {
   DevBuf scratch;
   Scratch* host_sc = nullptr;  // pinned mirror
   DevBuf stage_buf, iso_buf, seg_buf;
+  DevBuf tkeys, wtab, ostage;   // indexed face set: triangle edge keys, weld table, host-delivery staging
+  long long tkeys_cap = 0;
   McConst mc;
   // timing
   bool timing = false;
@@ -294,7 +300,8 @@ void amr_destroy(amr_ctx* c) {
   else cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
                     &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals, &c->scratch,
-                    &c->stage_buf, &c->iso_buf, &c->seg_buf};
+                    &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->tkeys, &c->wtab,
+                    &c->ostage};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
   for (auto& v : c->pending)
@@ -325,6 +332,10 @@ int amr_trim(amr_ctx* c) {
   release(c->staging);
   release(c->codes);
   release(c->stage_buf);
+  release(c->tkeys);
+  release(c->wtab);
+  release(c->ostage);
+  c->tkeys_cap = 0;
   return AMR_OK;
 }
 
@@ -435,13 +446,15 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   if (c->n_slots) {
     const Locator L = make_locator(c);
     // binned placement unless asked otherwise or the input is small
-    c->placement = binned ? (codes ? 2 : 1) : 0;
-    if (binned) {
+    // binned placement needs the insert pass's cell codes; a table too large
+    // for them (after rebuilds) falls back to the direct scatter
+    c->placement = binned && codes ? 1 : 0;
+    if (binned && codes) {
       AMR_TRY(ensure(c->staging, bin_layout(c->n_slots).bytes));
       {
         KernelTimer kt(c, KT_BIN);
-        AMR_CUDA(launch_bin_coarse(logb, c->xyz, c->lvl, c->s, n, L, c->n_slots, c->staging.p, dev_sc(c),
-                                   c->sm_count, codes, c->stream));
+        AMR_CUDA(launch_bin_coarse(logb, c->s, n, L, c->n_slots, c->staging.p, dev_sc(c), c->sm_count, codes,
+                                   c->stream));
       }
       {
         KernelTimer kt(c, KT_BIN_FINE);
@@ -609,6 +622,146 @@ int amr_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t* n_tris, in
   return nt > cap ? AMR_ERR_CAPACITY : AMR_OK;
 }
 
+int amr_iso_indexed(amr_ctx* c, float iso, float* vtx, int64_t vcap, int32_t* tri, int64_t tcap, int32_t* vkeys,
+                    int64_t* n_vtx, int64_t* n_tri, int flags) {
+  if (!c || !n_vtx || !n_tri || vcap < 0 || tcap < 0 || (vcap > 0 && !vtx) || (tcap > 0 && !tri))
+    return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  const Locator L = make_locator(c);
+  const uint4* du = static_cast<const uint4*>(c->duals.p);
+  unsigned long long* counter = &dev_sc(c)->n_tri[0];
+  // 1. the kept triangles' edge keys (rerun once with the exact count if short)
+  long long kcap = std::max(c->tkeys_cap, c->n_dual / 4 + 1024);
+  long long nt = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    AMR_TRY(ensure(c->tkeys, (size_t)kcap * 24));
+    c->tkeys_cap = (long long)(c->tkeys.bytes / 24);
+    AMR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), c->stream));
+    {
+      KernelTimer kt(c, KT_MC_KEYS);
+      AMR_CUDA(launch_mc_keys(c->logb, L, du, c->n_dual, iso, static_cast<unsigned long long*>(c->tkeys.p),
+                              c->tkeys_cap, counter, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream));
+    }
+    AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             c->stream));
+    AMR_CUDA(cudaStreamSynchronize(c->stream));
+    nt = (long long)c->host_sc->n_tri[0];
+    if (nt <= c->tkeys_cap) break;
+    kcap = nt;
+  }
+  if (nt > c->tkeys_cap) return AMR_ERR_CUDA;
+  // outputs: the caller's device buffers, or staging for host delivery
+  const bool host = (flags & AMR_HOST_PTRS) != 0;
+  const size_t vbytes = (size_t)vcap * 12, kbytes = vkeys ? (size_t)vcap * 8 : 0, tbytes = (size_t)tcap * 12;
+  float* dv = vtx;
+  int* dk = vkeys;
+  int* dt = tri;
+  if (host) {
+    AMR_TRY(ensure(c->ostage, vbytes + kbytes + tbytes + 16));
+    unsigned char* b = static_cast<unsigned char*>(c->ostage.p);
+    dv = reinterpret_cast<float*>(b);
+    dk = vkeys ? reinterpret_cast<int*>(b + vbytes) : nullptr;
+    dt = reinterpret_cast<int*>(b + vbytes + kbytes);
+  }
+  // 2. weld: table sized for up to nt distinct vertices at half load (a closed
+  //    surface has about nt / 2), rebuilt four times larger if it fills up
+  unsigned long long want = pow2_at_least((unsigned long long)std::max(2 * nt, 1024ll));
+  long long nv = 0;
+  for (int attempt = 0;; ++attempt) {
+    AMR_TRY(ensure(c->wtab, (size_t)want * 16));
+    AMR_CUDA(cudaMemsetAsync(c->wtab.p, 0xFF, (size_t)want * 16, c->stream));
+    AMR_TRY(reset_scratch(c));
+    {
+      KernelTimer kt(c, KT_WELD_INSERT);
+      AMR_CUDA(launch_weld_insert(c->logb, L, static_cast<const unsigned long long*>(c->tkeys.p), 3 * nt,
+                                  static_cast<ulonglong2*>(c->wtab.p), want - 1, iso, dv, dk, vcap, dev_sc(c),
+                                  grid_for(c, 3 * nt, 256, 8), c->stream));
+    }
+    AMR_TRY(read_scratch(c));
+    if (c->host_sc->err & ERR_HASH_FULL) {
+      if (attempt >= 3) return AMR_ERR_RANGE;
+      want *= 4;
+      continue;
+    }
+    nv = (long long)c->host_sc->n_vtx;
+    break;
+  }
+  // 3. the triangles' vertex indices
+  {
+    KernelTimer kt(c, KT_WELD_INDEX);
+    AMR_CUDA(launch_weld_index(static_cast<const unsigned long long*>(c->tkeys.p), std::min<long long>(nt, tcap),
+                               static_cast<const ulonglong2*>(c->wtab.p), want - 1, dt,
+                               grid_for(c, 3 * std::min<long long>(nt, tcap), 256, 8), c->stream));
+  }
+  *n_vtx = nv;
+  *n_tri = nt;
+  if (host) {
+    const long long wv = std::min(nv, (long long)vcap), wt = std::min(nt, (long long)tcap);
+    if (wv > 0) AMR_TRY(deliver(c, vtx, dv, (size_t)wv * 12, flags));
+    if (wv > 0 && vkeys) AMR_TRY(deliver(c, vkeys, dk, (size_t)wv * 8, flags));
+    if (wt > 0) AMR_TRY(deliver(c, tri, dt, (size_t)wt * 12, flags));
+  }
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  return (nv > vcap || nt > tcap) ? AMR_ERR_CAPACITY : AMR_OK;
+}
+
+int amr_interpolate(amr_ctx* c, float iso, const float* attr, const int32_t* vkeys, int64_t nv, float* out,
+                    int flags) {
+  if (!c || nv < 0 || (nv > 0 && (!attr || !vkeys || !out))) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 1) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  if (nv == 0) return AMR_OK;
+  const float* da = attr;
+  const int* dk = vkeys;
+  float* dout = out;
+  const bool host = (flags & AMR_HOST_PTRS) != 0;
+  if (host) {   // staging: attribute per cell, keys and results per vertex
+    const size_t abytes = (size_t)c->n * 4, kbytes = (size_t)nv * 8;
+    AMR_TRY(ensure(c->ostage, abytes + kbytes + (size_t)nv * 4 + 16));
+    unsigned char* b = static_cast<unsigned char*>(c->ostage.p);
+    AMR_CUDA(cudaMemcpyAsync(b, attr, abytes, cudaMemcpyHostToDevice, c->stream));
+    AMR_CUDA(cudaMemcpyAsync(b + abytes, vkeys, kbytes, cudaMemcpyHostToDevice, c->stream));
+    da = reinterpret_cast<const float*>(b);
+    dk = reinterpret_cast<const int*>(b + abytes);
+    dout = reinterpret_cast<float*>(b + abytes + kbytes);
+  }
+  AMR_TRY(reset_scratch(c));
+  {
+    KernelTimer kt(c, KT_INTERPOLATE);
+    AMR_CUDA(launch_interpolate(c->xyz, c->s, da, c->n, dk, nv, iso, dout, dev_sc(c), grid_for(c, nv, 256, 8),
+                                c->stream));
+  }
+  if (host) AMR_TRY(deliver(c, out, dout, (size_t)nv * 4, flags));
+  AMR_TRY(read_scratch(c));
+  return err_code(c->host_sc->err);
+}
+
+int amr_dual_shapes(amr_ctx* c, uint8_t* counts, int64_t* hist, int flags) {
+  if (!c || (!counts && !hist)) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  const long long nd = c->n_dual;
+  unsigned char* dc = counts ? reinterpret_cast<unsigned char*>(counts) : nullptr;
+  const bool host = (flags & AMR_HOST_PTRS) != 0;
+  AMR_TRY(ensure(c->ostage, (size_t)(host && counts ? nd : 0) + 16 * 9));
+  unsigned long long* dh = static_cast<unsigned long long*>(c->ostage.p);
+  if (host && counts) dc = static_cast<unsigned char*>(c->ostage.p) + 16 * 9;
+  AMR_CUDA(cudaMemsetAsync(dh, 0, 9 * sizeof(unsigned long long), c->stream));
+  {
+    KernelTimer kt(c, KT_SHAPES);
+    AMR_CUDA(launch_dual_shapes(static_cast<const uint4*>(c->duals.p), nd, dc, dh, grid_for(c, nd, 256, 8),
+                                c->stream));
+  }
+  if (host && counts && nd > 0) AMR_TRY(deliver(c, counts, dc, (size_t)nd, flags));
+  unsigned long long hh[9];
+  AMR_CUDA(cudaMemcpyAsync(hh, dh, sizeof(hh), cudaMemcpyDeviceToHost, c->stream));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  if (hist)
+    for (int k = 0; k < 9; ++k) hist[k] = (int64_t)hh[k];
+  return AMR_OK;
+}
+
 int amr_iso_cases(amr_ctx* c, float iso, uint8_t* cases, uint8_t* ntri, int flags) {
   if (!c || (!cases && !ntri)) return AMR_ERR_INVALID_ARG;
   if (c->stage < 3) return AMR_ERR_STATE;
@@ -718,7 +871,8 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->reserved = 0;
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
                           &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals,
-                          &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf};
+                          &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->tkeys, &c->wtab,
+                          &c->ostage};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);
   info->device_bytes = total;

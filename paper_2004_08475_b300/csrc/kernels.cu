@@ -412,14 +412,13 @@ __device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gb
   return total;
 }
 
-// With codes (from k_insert_bricks: table entry << 3 LOGB | Morton index of
-// the cell in its brick), a cell's slot is one table read away; without,
-// the cell's key is formed and looked up again.
-template <int LOGB, bool CODED>
-__global__ void __launch_bounds__(kCoarseThreads) k_bin_coarse(
-    const int* __restrict__ xyz, const unsigned char* __restrict__ lvl, const float* __restrict__ s,
-    long long n, Locator L, int n_coarse, Stage A, unsigned* __restrict__ coarse_count, Scratch* sc,
-    const unsigned* __restrict__ codes) {
+// A cell's slot is one table read away: its code (from k_insert_bricks)
+// holds the table entry of its brick << 3 LOGB | its Morton index there.
+template <int LOGB>
+__global__ void __launch_bounds__(kCoarseThreads) k_bin_coarse(const float* __restrict__ s, long long n, Locator L,
+                                                               int n_coarse, Stage A,
+                                                               unsigned* __restrict__ coarse_count, Scratch* sc,
+                                                               const unsigned* __restrict__ codes) {
   extern __shared__ unsigned smem[];
   unsigned* start = smem;                     // [n_coarse] counts, then run starts in the tile
   unsigned* gbase = start + n_coarse;         // [n_coarse] run starts in the bins
@@ -434,64 +433,24 @@ __global__ void __launch_bounds__(kCoarseThreads) k_bin_coarse(
     for (int b = t; b < n_coarse; b += kCoarseThreads) start[b] = 0;
     __syncthreads();
     unsigned slot[kCoarsePer], rank[kCoarsePer], val[kCoarsePer];
-    if (CODED) {
 #pragma unroll
-      for (int j = 0; j < kCoarsePer; ++j) {
-        const long long i = tile0 + (long long)j * kCoarseThreads + t;
-        slot[j] = kReject;
-        rank[j] = 0;
-        val[j] = 0u;
-        if (i < n) {
-          const unsigned c = __ldcs(codes + i);
-          const float v = __ldcs(s + i);
-          if (!isfinite(v)) err |= ERR_NONFINITE;
-          val[j] = __float_as_uint(v);
-          const unsigned bi = (unsigned)__ldg(&L.htab[c >> (3 * LOGB)].y);
-          slot[j] = (bi << (3 * LOGB)) | (c & ((1u << (3 * LOGB)) - 1u));
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kCoarsePer; ++j)
-        if (slot[j] != kReject) rank[j] = atomicAdd(&start[slot[j] >> kCoarseShift], 1u);
-    }
-#pragma unroll
-    for (int h = 0; h < (CODED ? 0 : kCoarsePer); h += 4) {   // four cells at a time, first probes together
-      int loc[4];
-      unsigned long long key[4];
-      int b0[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const long long i = tile0 + (long long)(h + u) * kCoarseThreads + t;
-        key[u] = kEmptyKey;
-        loc[u] = 0;
-        val[h + u] = 0u;
-        if (i < n) {
-          const int x = __ldcs(xyz + 3 * i), y = __ldcs(xyz + 3 * i + 1), z = __ldcs(xyz + 3 * i + 2);
-          const int l = __ldcs(lvl + i);
-          const float v = __ldcs(s + i);
-          if (!isfinite(v)) err |= ERR_NONFINITE;
-          val[h + u] = __float_as_uint(v);
-          if (l <= kMaxLevel) {
-            key[u] = brick_key<LOGB>(x, y, z, l);
-            loc[u] = (int)local_index<LOGB>(x, y, z, l);
-          }
-        }
-        b0[u] = key[u] != kEmptyKey ? probe_home(L, key[u]) : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        slot[h + u] = kReject;
-        rank[h + u] = 0;
-        if (key[u] == kEmptyKey) continue;
-        const int bi = b0[u] != -2 ? b0[u] : find_brick(L, key[u]);
-        if (bi < 0) {
-          err |= ERR_HASH_FULL;
-          continue;
-        }
-        slot[h + u] = ((unsigned)bi << (3 * LOGB)) | (unsigned)loc[u];
-        rank[h + u] = atomicAdd(&start[slot[h + u] >> kCoarseShift], 1u);
+    for (int j = 0; j < kCoarsePer; ++j) {
+      const long long i = tile0 + (long long)j * kCoarseThreads + t;
+      slot[j] = kReject;
+      rank[j] = 0;
+      val[j] = 0u;
+      if (i < n) {
+        const unsigned c = __ldcs(codes + i);
+        const float v = __ldcs(s + i);
+        if (!isfinite(v)) err |= ERR_NONFINITE;
+        val[j] = __float_as_uint(v);
+        const unsigned bi = (unsigned)__ldg(&L.htab[c >> (3 * LOGB)].y);
+        slot[j] = (bi << (3 * LOGB)) | (c & ((1u << (3 * LOGB)) - 1u));
       }
     }
+#pragma unroll
+    for (int j = 0; j < kCoarsePer; ++j)
+      if (slot[j] != kReject) rank[j] = atomicAdd(&start[slot[j] >> kCoarseShift], 1u);
     __syncthreads();
     const unsigned total = scan_and_reserve<kMaxCoarse / kCoarseThreads>(start, gbase, n_coarse, coarse_count, 0,
                                                                          wsum);
@@ -896,29 +855,6 @@ __device__ __forceinline__ void write_triangles(const int4* __restrict__ bricks,
   }
 }
 
-// Same triangles into a contiguous buffer (no capacity check): out[9 t'...]
-// for the t'-th kept triangle.
-template <int LOGB>
-__device__ __forceinline__ void stage_triangles(const int4* __restrict__ bricks, const unsigned* vr,
-                                                const float* sr, float iso, unsigned long long packed,
-                                                unsigned keep, float* out, unsigned long long ea,
-                                                unsigned long long eb) {
-  for (int t = 0; t < 5; ++t) {
-    if (!((keep >> t) & 1u)) continue;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int k = (int)((packed >> (12 * t + 4 * c)) & 15);
-      const int a = (int)((ea >> (4 * k)) & 15), b = (int)((eb >> (4 * k)) & 15);
-      const float3 q = edge_vertex(slot_cell<LOGB>(bricks, vr[a]), sr[a], slot_cell<LOGB>(bricks, vr[b]), sr[b],
-                                   iso);
-      out[3 * c + 0] = q.x;
-      out[3 * c + 1] = q.y;
-      out[3 * c + 2] = q.z;
-    }
-    out += 9;
-  }
-}
-
 constexpr int kRow = 9;   // shared-memory row stride (words): conflict-free across a warp
 constexpr int kTriStage = 80;   // triangles a warp stages in shared memory per step
 
@@ -1253,7 +1189,15 @@ constexpr int kMcSmemBytes = 4 * (kMcRowsWords + 8 * kTriStage + 8 * kTriStage *
 // triangles; the warp's 32 lanes take the step's 3T vertices in turn, stage
 // them, and write the step's triangles as one coalesced run. Optionally
 // writes per-dual case and triangle count instead.
-template <int LOGB, bool EMIT, bool CASES>
+// Edge key of a triangle vertex: the unordered pair of slots it interpolates
+// between (slots stay below 2^31), smaller first.
+__device__ __forceinline__ unsigned long long slot_pair(unsigned a, unsigned b) {
+  return a < b ? ((unsigned long long)a << 32) | b : ((unsigned long long)b << 32) | a;
+}
+
+// KEYS: instead of vertex positions, each triangle's 3 edge keys (u64) go to
+// tris reinterpreted as [cap][3] u64 (for the indexed face set).
+template <int LOGB, bool EMIT, bool CASES, bool KEYS = false>
 __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
                                             float iso, float* __restrict__ tris, long long cap,
                                             unsigned long long* counter, unsigned char* cases,
@@ -1322,15 +1266,45 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
           const int k = (int)((ent >> (8 + 4 * c)) & 15u);
           const int a = (int)((mc.edge_a >> (4 * k)) & 15), b = (int)((mc.edge_b >> (4 * k)) & 15);
           const unsigned va = rv[a], vb = rv[b];   // scalars gathered again: just read, so cached
-          const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, va), __ldg(L.scal + va),
-                                       slot_cell<LOGB>(L.bricks, vb), __ldg(L.scal + vb), iso);
-          wst[3 * q] = p.x;
-          wst[3 * q + 1] = p.y;
-          wst[3 * q + 2] = p.z;
+          if (KEYS) {
+            reinterpret_cast<unsigned long long*>(wst)[q] = slot_pair(va, vb);
+          } else {
+            const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, va), __ldg(L.scal + va),
+                                         slot_cell<LOGB>(L.bricks, vb), __ldg(L.scal + vb), iso);
+            wst[3 * q] = p.x;
+            wst[3 * q + 1] = p.y;
+            wst[3 * q + 2] = p.z;
+          }
         }
         __syncwarp();
-        const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
-        for (long long k = lane; k < lim; k += 32) tris[9 * first + k] = wst[k];
+        if (KEYS) {
+          const long long lim = min((long long)total, cap - first) * 3;
+          unsigned long long* out = reinterpret_cast<unsigned long long*>(tris) + 3 * first;
+          for (long long k = lane; k < lim; k += 32) out[k] = reinterpret_cast<const unsigned long long*>(wst)[k];
+        } else {
+          const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
+          for (long long k = lane; k < lim; k += 32) tris[9 * first + k] = wst[k];
+        }
+        __syncwarp();
+      } else if (KEYS) {   // more triangles than the stage holds: each lane writes its own keys
+        unsigned long long* out = reinterpret_cast<unsigned long long*>(tris);
+        const unsigned long long kp[2] = {sh.packed[c0], sh.packed[c1]};
+        const unsigned km[2] = {k0, k1};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const unsigned* rv = r0 + 32 * kRow * j;
+          for (int t = 0; t < 5; ++t) {
+            if (!((km[j] >> t) & 1u)) continue;
+            if (idx < cap) {
+#pragma unroll
+              for (int cc = 0; cc < 3; ++cc) {
+                const int kk = (int)((kp[j] >> (12 * t + 4 * cc)) & 15);
+                out[3 * idx + cc] = slot_pair(rv[(mc.edge_a >> (4 * kk)) & 15], rv[(mc.edge_b >> (4 * kk)) & 15]);
+              }
+            }
+            ++idx;
+          }
+        }
         __syncwarp();
       } else {   // more triangles than the stage holds: each lane writes its own (scalars in the stage)
         float* q0 = wst + lane * 2 * kRow;
@@ -1349,6 +1323,83 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
         __syncwarp();
       }
     }
+  }
+}
+
+// Indexed face set, welding pass: every triangle vertex's edge key goes into
+// a hash table (16-byte entries {key, vertex index}, Fibonacci home, linear
+// probing); the thread whose CAS places a key numbers the vertex (one atomic
+// per warp), computes its position once and records its cells' input
+// indices. A probe run longer than `limit` sets ERR_HASH_FULL (the host
+// rebuilds the table larger).
+template <int LOGB>
+__global__ void __launch_bounds__(256) k_weld_insert(Locator L, const unsigned long long* __restrict__ tkeys,
+                                                     long long n_keys, ulonglong2* wtab, unsigned long long wmask,
+                                                     float iso, float* __restrict__ vtx, int* __restrict__ vkeys,
+                                                     long long vcap, Scratch* sc) {
+  const unsigned long long limit = wmask < 4095ull ? wmask + 1 : 4096ull;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long nk = (n_keys + 31) & ~31ll;   // whole warps, for the warp-wide append
+  unsigned err = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += stride) {
+    const bool live = i < n_keys;
+    const unsigned long long key = live ? __ldcs(tkeys + i) : kEmptyKey;
+    bool won = false;
+    unsigned long long h = 0;
+    if (live) {
+      h = home_of(key, wmask);
+      bool done = false;
+      for (unsigned long long p = 0; p < limit; ++p) {
+        const unsigned long long c = __ldcg(&wtab[h].x);
+        if (c == key) { done = true; break; }
+        if (c == kEmptyKey) {
+          const unsigned long long prev = atomicCAS(&wtab[h].x, kEmptyKey, key);
+          if (prev == kEmptyKey) { won = true; done = true; break; }
+          if (prev == key) { done = true; break; }
+        }
+        h = (h + 1) & wmask;
+      }
+      if (!done) err |= ERR_HASH_FULL;
+    }
+    const long long vid = warp_append(won ? 1u : 0u, &sc->n_vtx);
+    if (won) {
+      wtab[h].y = (unsigned long long)vid;
+      if (vid < vcap) {
+        const unsigned va = (unsigned)(key >> 32), vb = (unsigned)key;
+        const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, va), __ldg(L.scal + va),
+                                     slot_cell<LOGB>(L.bricks, vb), __ldg(L.scal + vb), iso);
+        vtx[3 * vid] = p.x;
+        vtx[3 * vid + 1] = p.y;
+        vtx[3 * vid + 2] = p.z;
+        if (vkeys) {   // the edge's two cells as input indices, smaller first
+          const int ia = (int)(unsigned)__ldg(L.rec + va), ib = (int)(unsigned)__ldg(L.rec + vb);
+          vkeys[2 * vid] = min(ia, ib);
+          vkeys[2 * vid + 1] = max(ia, ib);
+        }
+      }
+    }
+  }
+  err = warp_or(err);
+  if ((threadIdx.x & 31) == 0 && err) atomicOr(&sc->err, err);
+}
+
+// Indexed face set, index pass: each triangle's three keys looked up in the
+// completed table.
+__global__ void __launch_bounds__(256) k_weld_index(const unsigned long long* __restrict__ tkeys, long long n_tri,
+                                                    const ulonglong2* __restrict__ wtab, unsigned long long wmask,
+                                                    int* __restrict__ tri) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_tri; i += stride) {
+    const unsigned long long key = __ldcs(tkeys + i);
+    unsigned long long h = home_of(key, wmask);
+    int vid = -1;
+    for (unsigned long long p = 0; p <= wmask; ++p) {   // every key is in the table
+      const ulonglong2 e = __ldg(wtab + h);
+      if (e.x == key) { vid = (int)e.y; break; }
+      if (e.x == kEmptyKey) break;
+      h = (h + 1) & wmask;
+    }
+    tri[i] = vid;
   }
 }
 
@@ -1598,23 +1649,18 @@ Stages stages_of(const BinLayout& lay, void* staging) {
 }
 }  // namespace
 
-cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
-                              Locator loc, long long n_slots, void* staging, Scratch* sc, int sm_count,
-                              const unsigned* codes, cudaStream_t st) {
+cudaError_t launch_bin_coarse(int logb, const float* s, long long n, Locator loc, long long n_slots, void* staging,
+                              Scratch* sc, int sm_count, const unsigned* codes, cudaStream_t st) {
   const BinLayout lay = bin_layout(n_slots);
   if (n_slots <= 0) return cudaSuccess;
-  if (lay.n_coarse > kMaxCoarse || n > 0xFFFFFFFFll) return cudaErrorInvalidValue;
+  if (lay.n_coarse > kMaxCoarse || n > 0xFFFFFFFFll || !codes) return cudaErrorInvalidValue;
   const Stages S = stages_of(lay, staging);
   cudaError_t e = cudaMemsetAsync(S.coarse_count, 0, 4 * (size_t)(lay.n_coarse + lay.n_win), st);
   if (e != cudaSuccess) return e;
   // dynamic shared memory above the 48 KB default (an attribute of the
   // current device's context, so set on every build)
-  if ((e = cudaFuncSetAttribute(k_bin_coarse<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSmemCoarse)) ||
-      (e = cudaFuncSetAttribute(k_bin_coarse<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSmemCoarse)) ||
-      (e = cudaFuncSetAttribute(k_bin_coarse<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
-      (e = cudaFuncSetAttribute(k_bin_coarse<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
+  if ((e = cudaFuncSetAttribute(k_bin_coarse<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
+      (e = cudaFuncSetAttribute(k_bin_coarse<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
       (e = cudaFuncSetAttribute(k_bin_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFine)) ||
       (e = cudaFuncSetAttribute(k_place_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)))
     return e;
@@ -1623,17 +1669,12 @@ cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl
   const int smem_coarse = (2 * (int)lay.n_coarse + 3 * kCoarseTile) * 4;   // kSmemCoarse at most
   AMR_DISPATCH(logb, ({
     int per_sm = 0;   // one resident wave: the tile loop is grid-strided
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, codes ? k_bin_coarse<LB, true> : k_bin_coarse<LB, false>, kCoarseThreads, smem_coarse)) !=
-        cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_coarse<LB>, kCoarseThreads,
+                                                           smem_coarse)) != cudaSuccess)
       return e;
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count * std::max(per_sm, 1));
-    if (codes)
-      k_bin_coarse<LB, true><<<grid, kCoarseThreads, smem_coarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse, S.a,
-                                                                     S.coarse_count, sc, codes);
-    else
-      k_bin_coarse<LB, false><<<grid, kCoarseThreads, smem_coarse, st>>>(xyz, lvl, s, n, loc, (int)lay.n_coarse,
-                                                                      S.a, S.coarse_count, sc, nullptr);
+    k_bin_coarse<LB><<<grid, kCoarseThreads, smem_coarse, st>>>(s, n, loc, (int)lay.n_coarse, S.a, S.coarse_count,
+                                                                sc, codes);
   }));
   return cudaGetLastError();
 }
@@ -1708,6 +1749,36 @@ cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, f
                                                              mc);
     }));
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mc_keys(int logb, Locator loc, const uint4* duals, long long nd, float iso,
+                           unsigned long long* tkeys, long long cap, unsigned long long* counter, const McConst& mc,
+                           int grid, cudaStream_t st) {
+  if (nd <= 0) return cudaSuccess;
+  AMR_DISPATCH(logb, ({
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_mc<LB, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMcSmemBytes);
+    if (e != cudaSuccess) return e;
+    k_mc<LB, true, false, true><<<grid, 256, kMcSmemBytes, st>>>(loc, duals, nd, iso, reinterpret_cast<float*>(tkeys),
+                                                                  cap, counter, nullptr, nullptr, mc);
+  }));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weld_insert(int logb, Locator loc, const unsigned long long* tkeys, long long n_keys,
+                               ulonglong2* wtab, unsigned long long wmask, float iso, float* vtx, int* vkeys,
+                               long long vcap, Scratch* sc, int grid, cudaStream_t st) {
+  if (n_keys <= 0) return cudaSuccess;
+  AMR_DISPATCH(logb, (k_weld_insert<LB><<<grid, 256, 0, st>>>(loc, tkeys, n_keys, wtab, wmask, iso, vtx, vkeys, vcap,
+                                                               sc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weld_index(const unsigned long long* tkeys, long long n_tri, const ulonglong2* wtab,
+                              unsigned long long wmask, int* tri, int grid, cudaStream_t st) {
+  if (n_tri <= 0) return cudaSuccess;
+  k_weld_index<<<grid, 256, 0, st>>>(tkeys, n_tri, wtab, wmask, tri);
   return cudaGetLastError();
 }
 

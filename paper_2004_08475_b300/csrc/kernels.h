@@ -30,6 +30,7 @@ struct Scratch {
   unsigned long long tile;              // persistent-kernel work counter
   unsigned long long n_tri[kMaxIso];    // per iso-value triangle counters
   unsigned long long n_occupied;        // occupied brick slots (= cells unless duplicates)
+  unsigned long long n_vtx;             // welded vertices of an indexed face set
   unsigned int err;
   int lo[3];                            // bounding box: min lower corner
   int hi[3];                            // max (lower corner + width)
@@ -87,9 +88,9 @@ struct BinLayout {
   size_t bytes = 0;
 };
 BinLayout bin_layout(long long n_slots);
-cudaError_t launch_bin_coarse(int logb, const int* xyz, const unsigned char* lvl, const float* s, long long n,
-                              Locator loc, long long n_slots, void* staging, Scratch* sc, int sm_count,
-                              const unsigned* codes, cudaStream_t st);
+// codes: from launch_insert_bricks (required).
+cudaError_t launch_bin_coarse(int logb, const float* s, long long n, Locator loc, long long n_slots, void* staging,
+                              Scratch* sc, int sm_count, const unsigned* codes, cudaStream_t st);
 cudaError_t launch_bin_fine(long long n_slots, void* staging, Scratch* sc, cudaStream_t st);
 cudaError_t launch_place_windows(long long n_slots, void* staging, unsigned long long* rec, cudaStream_t st);
 
@@ -115,6 +116,20 @@ cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, f
                       float* tris, long long cap, unsigned long long* counter,
                       unsigned char* cases, unsigned char* ntri, const McConst& mc, int grid,
                       cudaStream_t st);
+
+// Indexed face set (three passes): the kept triangles' edge keys (u64 slot
+// pairs, smaller first) into tkeys[cap][3] through `counter`; the keys into
+// the weld table wtab (all ones before the first pass; sc->n_vtx counts the
+// vertices, whose positions go to vtx[vcap][3] and cells' input indices to
+// vkeys[vcap][2] if not NULL); then tri[n_tri][3] vertex indices.
+cudaError_t launch_mc_keys(int logb, Locator loc, const uint4* duals, long long nd, float iso,
+                           unsigned long long* tkeys, long long cap, unsigned long long* counter, const McConst& mc,
+                           int grid, cudaStream_t st);
+cudaError_t launch_weld_insert(int logb, Locator loc, const unsigned long long* tkeys, long long n_keys,
+                               ulonglong2* wtab, unsigned long long wmask, float iso, float* vtx, int* vkeys,
+                               long long vcap, Scratch* sc, int grid, cudaStream_t st);
+cudaError_t launch_weld_index(const unsigned long long* tkeys, long long n_tri, const ulonglong2* wtab,
+                              unsigned long long wmask, int* tri, int grid, cudaStream_t st);
 
 cudaError_t launch_mc_batch_count(int logb, Locator loc, const uint4* duals, long long nd,
                                   const float* isos, int n_iso, Scratch* sc, const McConst& mc,

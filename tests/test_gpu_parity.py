@@ -87,6 +87,33 @@ def test_partitioned_duplicate_detected():
     assert e.value.code == amriso.ERR_DUPLICATE
 
 
+def test_placement_paths_agree_and_are_reported():
+    """From 2^20 cells on the default placement is binned, below it a direct
+    scatter; both give the same dual list and triangles."""
+    from paper_2004_08475_b300 import amriso
+    xyz, lv, s, iso, info = synth.uniform_grid(104, field="sphere")   # 1,124,864 cells
+    assert xyz.shape[0] >= 1 << 20
+    out = {}
+    for part in (0, -1):
+        ctx = amriso.AmrContext()
+        ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+        ctx.build_locator(partitioned=part)
+        out[part] = (ctx.info().placement, ctx.dual_cells(), ctx.get_duals().cpu().numpy(),
+                     canonical(ctx.iso(iso).cpu().numpy()))
+        ctx.close()
+    assert out[0][0] == 1 and out[-1][0] == 0
+
+    def rows_sorted(d):   # brick numbering (hence dual order) differs between builds
+        return d[np.lexsort(d.T[::-1])]
+    assert out[0][1] == out[-1][1] and np.array_equal(rows_sorted(out[0][2]), rows_sorted(out[-1][2]))
+    assert np.array_equal(out[0][3].view(np.int32), out[-1][3].view(np.int32))
+    small = synth.sphere_tiny()
+    ctx = amriso.AmrContext()
+    ctx.upload(small[0].cuda(), small[1].cuda(), small[2].cuda())
+    ctx.build_locator()
+    assert ctx.info().placement == 0
+
+
 def test_trim_keeps_results():
     """amr_trim frees the placement workspace; the resident locator and dual
     cells still give the same triangles."""

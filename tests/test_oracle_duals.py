@@ -133,3 +133,27 @@ def test_snap_levels():
         want = vox[p[2], p[1], p[0]]
         got = m.snap(*(p + lo))
         assert got == want
+
+
+def test_dual_shapes_pins():
+    """Shapes of the snapped duals (Sec. 4.1): a uniform grid gives only
+    hexahedra; the hand-derived two-level example gives one hexahedron and
+    one pyramid (5 distinct cells); on random octrees no emitted dual
+    collapses below 2 distinct cells (a level-l-owned dual reaches at least
+    one other cell), and shapes appear only at level changes."""
+    xyz, lv, s, iso, info = synth.uniform_grid(5, 1, (0, 0, 0))
+    xyz, lv = _np(xyz, lv)
+    assert (oracle.dual_shapes(oracle.OracleMesh(xyz, lv).duals()) == 8).all()
+    with open(os.path.join(GOLDEN, "two_level_pyramid.json")) as f:
+        g = json.load(f)
+    m = oracle.OracleMesh(np.array(g["xyz"], dtype=np.int32), np.array(g["level"], dtype=np.uint8))
+    assert sorted(oracle.dual_shapes(m.duals()).tolist()) == [5, 8]
+    for seed in range(4):
+        xyz, lv, s, iso, info = synth.random_octree(40 + seed, levels=3, roots=3, p_split=0.45, p_hole=0.0)
+        xyz, lv = _np(xyz, lv)
+        m = oracle.OracleMesh(xyz, lv)
+        d = m.duals()
+        k = oracle.dual_shapes(d)
+        assert k.min() >= 2 and (k == 8).any() and (k < 8).any()
+        same_level = np.array([len(set(lv[row].tolist())) == 1 for row in d])
+        assert (k[same_level] == 8).all()

@@ -292,3 +292,42 @@ def test_golden_pyramid_mc():
     assert r["tris"].shape[0] == g["n_triangles"]
     got = {tuple(v) for v in r["tris"].reshape(-1, 3).tolist()}
     assert got == {tuple(v) for v in g["triangle_vertices"]}
+
+
+def test_weld_sphere_indexed_face_set():
+    """The oracle's indexed face set (Sec. 5.2, vertices identified by edge
+    key): it reproduces every fat triangle bit for bit, has one vertex per
+    sign-changing dual edge, and is a closed sphere (V - E + F = 2)."""
+    xyz, lv, s, iso, m, d, r = _run(synth.sphere_tiny())
+    vtx, tri, vkeys = oracle.weld(r["tris"], r["keys"])
+    assert np.array_equal(vtx[tri].view(np.int32), r["tris"].view(np.int32))
+    assert {tuple(k) for k in vkeys.tolist()} == _crossed_dual_edges(d, s, iso)
+    assert vtx.shape[0] < 3 * tri.shape[0] // 2   # vertices are shared
+    rep = manifold_report(tri)
+    assert rep["V"] - rep["E"] + rep["F"] == 2
+
+
+def test_weld_rejects_two_positions_for_one_key():
+    tris = np.zeros((2, 3, 3), np.float32)
+    keys = np.array([[[0, 1], [1, 2], [0, 2]], [[0, 1], [1, 3], [0, 3]]], np.int64)
+    oracle.weld(tris, keys)   # same positions: fine
+    tris[1, 0, 0] = 1.0       # key (0,1) now at two positions
+    with pytest.raises(oracle.OracleError):
+        oracle.weld(tris, keys)
+    v, t, k = oracle.weld(np.zeros((0, 3, 3), np.float32), np.zeros((0, 3, 2), np.int64))
+    assert v.shape == (0, 3) and t.shape == (0, 3) and k.shape == (0, 2)
+
+
+def test_interpolate_closed_forms():
+    """Interpolating the centres' x coordinate reproduces every vertex's x
+    bit for bit (the same formula on another field); interpolating the
+    scalar itself gives the iso-value within a few ulp."""
+    xyz, lv, s, iso, m, d, r = _run(synth.sphere_tiny())
+    vtx, tri, vkeys = oracle.weld(r["tris"], r["keys"])
+    x = np.asarray(xyz)
+    centre_x = (x[:, 0].astype(np.float32) + (np.float32(1) * (1 << np.asarray(lv).astype(np.int64))).astype(np.float32)
+                * np.float32(0.5)).astype(np.float32)
+    fx = oracle.interpolate(x, s, centre_x, vkeys, iso)
+    assert np.array_equal(fx.view(np.int32), vtx[:, 0].view(np.int32))
+    fs = oracle.interpolate(x, s, s, vkeys, iso)
+    assert np.abs(fs - np.float32(iso)).max() <= 8 * np.spacing(np.float32(abs(iso) + np.abs(np.asarray(s)).max()))
