@@ -56,12 +56,14 @@ WORKLOADS = {
 }
 
 
-def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int, placement: int = 0) -> float:
+def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int, placement: int = 0,
+                      log2_brick: int = 3) -> float:
     """Compulsory bytes per launch of each kernel under the library's data
     layout: what the kernel must read and write at least once. placement 1
     (binned): the insert pass records each cell's 4-byte table code and the
     coarse binning reads it instead of the cell's corner and level."""
     coded = placement == 1
+    b3 = 512.0 if log2_brick == 3 else 64.0
     return {
         "k_insert_bricks": 13.0 * n + (4.0 * n if coded else 0.0),   # xyz + level (+ code)
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
@@ -69,6 +71,9 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int, place
         "k_bin_fine": 12.0 * n + 12.0 * n,           # re-split the entries by window
         "k_place_windows": 12.0 * n + 8.0 * n_slots, # read the entries, write every slot's record
         "k_resolve_views": 16.0 * n_slots,           # read the record, write view + scalar
+        "k_order_count": 16.0 * n_slots / b3,        # read each brick's record
+        "k_order_scan": 8.0 * 32768,                 # read and write the bucket counters
+        "k_order_scatter": 20.0 * n_slots / b3,      # read each brick's record, write its position
         "k_dual_cells": 4.0 * n_slots + 32.0 * nd,   # read views once, write 8 slots / dual
         "k_mc": 32.0 * nd + 4.0 * n + 36.0 * nt,     # read tuples + scalars, write triangles
         # read views + scalars once, write the dual list and the triangles
@@ -87,7 +92,7 @@ def load_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.h"):
+    for f in ("kernels.cu", "kernels.h", "order.cu", "order.h"):
         with open(os.path.join(ROOT, "paper_2004_08475_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -434,7 +439,8 @@ def main():
 
     kt = {k: v for k, v in ktimes.items() if v[1] > 0}
     t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_bin_coarse", "k_bin_fine",
-                                               "k_place_windows", "k_resolve_views", "k_brick_neighbors")) / args.steps
+                                               "k_place_windows", "k_resolve_views", "k_brick_neighbors",
+                                               "k_order_count", "k_order_scan", "k_order_scatter")) / args.steps
     t_dual = (kt.get("k_dual_cells", (0, 1))[0] + kt.get("k_dual_cells_iso", (0, 1))[0]) / args.steps
     t_iso = kt.get("k_mc", (0, 1))[0] / args.steps
     launches = int(sum(v[1] for v in kt.values()))
@@ -445,7 +451,7 @@ def main():
     kernels = {}
     for k, (tot_ms, cnt) in kt.items():
         per = tot_ms / cnt
-        b = algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement)
+        b = algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement, inf.log2_brick)
         kernels[k] = {"ms_per_launch": per, "launches": cnt, "share": tot_ms / total_kms,
                       "algorithmic_bytes": b, "gbs": b / per / 1e6 if per > 0 else 0.0}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
@@ -457,8 +463,8 @@ def main():
                 "frac": dk["gbs"] / peak, "peak_source": peak_src,
                 "traffic": ncu_traffic(dom, args.workload, units),
                 "algorithmic_bytes_per_launch": dk["algorithmic_bytes"]}
-    step_bytes = sum(algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement) * v[1] / args.steps
-                     for k, v in kt.items())
+    step_bytes = sum(algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement, inf.log2_brick) * v[1]
+                     for k, v in kt.items()) / args.steps
 
     # batched multi-iso over the resident dual cells
     batch = None

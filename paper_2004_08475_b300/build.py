@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libamriso.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "attributes.cu", "shapes.cu", "mc_table.cpp"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "attributes.cu", "shapes.cu", "order.cu", "mc_table.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

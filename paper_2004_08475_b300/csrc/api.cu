@@ -13,6 +13,7 @@
 #include "kernels.h"
 #include "shapes.h"
 #include "mc_table.h"
+#include "order.h"
 
 using namespace amriso;
 
@@ -30,13 +31,13 @@ struct DevBuf {
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
   KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_BIN_FINE, KT_MC_KEYS, KT_WELD_INSERT,
-  KT_WELD_INDEX, KT_INTERPOLATE, KT_SHAPES, KT_COUNT
+  KT_WELD_INDEX, KT_INTERPOLATE, KT_SHAPES, KT_ORDER_COUNT, KT_ORDER_SCAN, KT_ORDER_SCATTER, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
     "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
     "k_bin_coarse", "k_place_windows", "k_dual_cells_iso", "k_bin_fine", "k_mc_keys", "k_weld_insert",
-    "k_weld_index", "k_interpolate", "k_dual_shapes"};
+    "k_weld_index", "k_interpolate", "k_dual_shapes", "k_order_count", "k_order_scan", "k_order_scatter"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -82,6 +83,7 @@ struct amr_ctx {
   int block = 256;
   int check_overlap = 0;
   DevBuf htab, bricks, rec, scal, view, nbr, staging, codes;
+  DevBuf border, bcount;   // bricks in spatial order (the dual pass's visiting order), bucket counters
   int placement = 0;   // 0 direct scatter, 1 binned
   unsigned long long hcap = 0;
   long long n_bricks = 0, n_slots = 0;
@@ -301,7 +303,7 @@ void amr_destroy(amr_ctx* c) {
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
                     &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals, &c->scratch,
                     &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->tkeys, &c->wtab,
-                    &c->ostage};
+                    &c->ostage, &c->border, &c->bcount};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
   for (auto& v : c->pending)
@@ -335,6 +337,7 @@ int amr_trim(amr_ctx* c) {
   release(c->tkeys);
   release(c->wtab);
   release(c->ostage);
+  release(c->bcount);
   c->tkeys_cap = 0;
   return AMR_OK;
 }
@@ -400,6 +403,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   want = std::min<unsigned long long>(want, 1ull << 22);
   const bool binned = partitioned > 0 || (partitioned == 0 && n >= kBinnedMinCells);
   unsigned* codes = nullptr;   // binned placement: each cell's table entry, recorded by the insert pass
+  OrderFrame frame{};          // bucket frame of the bricks' spatial order (from the bounding box)
   for (int attempt = 0;; ++attempt) {
     c->hcap = pow2_at_least(want);
     codes = nullptr;
@@ -436,6 +440,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
       if ((long long)h.hi[a] - (long long)h.lo[a] >= (1ll << 21) || h.lo[a] < -(1 << 30) ||
           h.hi[a] > (1 << 30))
         return AMR_ERR_RANGE;
+    if (n > 0) frame = order_frame(h.lo, h.hi);
     break;
   }
   c->n_slots = c->n_bricks * B3;
@@ -482,6 +487,25 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
       AMR_CUDA(launch_brick_neighbors(logb, L, c->n_bricks, static_cast<int*>(c->nbr.p),
                                       grid_for(c, c->n_bricks * 27, 256, 8), c->stream));
     }
+    // the dual pass visits the bricks bucket by bucket along a Morton curve
+    AMR_TRY(ensure(c->border, (size_t)c->n_bricks * 4));
+    AMR_TRY(ensure(c->bcount, (size_t)kOrderBuckets * 4));
+    unsigned* cnt = static_cast<unsigned*>(c->bcount.p);
+    AMR_CUDA(cudaMemsetAsync(cnt, 0, (size_t)kOrderBuckets * 4, c->stream));
+    {
+      KernelTimer kt(c, KT_ORDER_COUNT);
+      AMR_CUDA(launch_brick_order_count(L.bricks, c->n_bricks, frame, cnt, grid_for(c, c->n_bricks, 256, 8),
+                                        c->stream));
+    }
+    {
+      KernelTimer kt(c, KT_ORDER_SCAN);
+      AMR_CUDA(launch_brick_order_scan(cnt, c->stream));
+    }
+    {
+      KernelTimer kt(c, KT_ORDER_SCATTER);
+      AMR_CUDA(launch_brick_order_scatter(L.bricks, c->n_bricks, frame, cnt, static_cast<int*>(c->border.p),
+                                          grid_for(c, c->n_bricks, 256, 8), c->stream));
+    }
     AMR_TRY(read_scratch(c));
     const int rc = err_code(c->host_sc->err);
     if (rc != AMR_OK) return rc;
@@ -504,8 +528,9 @@ int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
     AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->n_dual, 0, sizeof(unsigned long long), c->stream));
     {
       KernelTimer kt(c, KT_DUAL);
-      AMR_CUDA(launch_dual_cells(c->logb, make_locator(c), static_cast<const int*>(c->nbr.p), c->n_bricks,
-                                 static_cast<uint4*>(c->duals.p), c->dual_cap, dev_sc(c), c->stream));
+      AMR_CUDA(launch_dual_cells(c->logb, make_locator(c), static_cast<const int*>(c->nbr.p),
+                                 static_cast<const int*>(c->border.p), c->n_bricks, static_cast<uint4*>(c->duals.p),
+                                 c->dual_cap, dev_sc(c), c->stream));
     }
     AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_dual, &dev_sc(c)->n_dual, sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, c->stream));
@@ -542,7 +567,8 @@ int amr_dual_cells_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t*
     AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->n_tri[0], 0, sizeof(unsigned long long), c->stream));
     {
       KernelTimer kt(c, KT_DUAL_ISO);
-      AMR_CUDA(launch_dual_cells_iso(c->logb, make_locator(c), static_cast<const int*>(c->nbr.p), c->n_bricks,
+      AMR_CUDA(launch_dual_cells_iso(c->logb, make_locator(c), static_cast<const int*>(c->nbr.p),
+                                     static_cast<const int*>(c->border.p), c->n_bricks,
                                      static_cast<uint4*>(c->duals.p), c->dual_cap, dev_sc(c), iso, dst, cap,
                                      c->mc, c->stream));
     }
@@ -872,7 +898,7 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
                           &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals,
                           &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->tkeys, &c->wtab,
-                          &c->ostage};
+                          &c->ostage, &c->border, &c->bcount};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);
   info->device_bytes = total;

@@ -903,8 +903,9 @@ struct DualShape {
 // triangles, bit for bit, as k_mc over the resident dual list.
 template <int LOGB, bool ISO>
 __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
-    Locator L, const int* __restrict__ nbr, long long n_bricks, uint4* __restrict__ duals, long long cap,
-    Scratch* sc, float iso, float* __restrict__ tris, long long tri_cap, const __grid_constant__ McConst mc) {
+    Locator L, const int* __restrict__ nbr, const int* __restrict__ order, long long n_bricks,
+    uint4* __restrict__ duals, long long cap, Scratch* sc, float iso, float* __restrict__ tris, long long tri_cap,
+    const __grid_constant__ McConst mc) {
   constexpr int B = 1 << LOGB;
   constexpr int R = B + 2;
   constexpr int NT = DualShape<LOGB>::kThreads;
@@ -945,7 +946,9 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
   }
   for (int row = t; row < R * R; row += NT) rmask[row] = 0;   // cleared again after each use
   __syncthreads();
-  for (long long bi = blockIdx.x; bi < n_bricks; bi += gridDim.x) {
+  for (int it = blockIdx.x; it < n_bricks; it += gridDim.x) {   // n_bricks * B^3 < 2^31
+    // bricks in the given spatial order (neighbours' halos then stay in L2)
+    const int bi = order ? __ldg(order + it) : it;
     const int4 b = __ldg(L.bricks + bi);
     const int l = b.w;
     bool mine[CPT];
@@ -1711,23 +1714,23 @@ cudaError_t launch_brick_neighbors(int logb, Locator loc, long long n_bricks, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, long long n_bricks, uint4* duals,
-                              long long cap, Scratch* sc, cudaStream_t st) {
+cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, const int* order, long long n_bricks,
+                              uint4* duals, long long cap, Scratch* sc, cudaStream_t st) {
   if (n_bricks <= 0) return cudaSuccess;
   const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
   McConst none{};
   AMR_DISPATCH(logb, (k_dual_cells<LB, false><<<grid, DualShape<LB>::kThreads, 0, st>>>(
-                         loc, nbr, n_bricks, duals, cap, sc, 0.f, nullptr, 0, none)));
+                         loc, nbr, order, n_bricks, duals, cap, sc, 0.f, nullptr, 0, none)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, long long n_bricks, uint4* duals,
-                                  long long cap, Scratch* sc, float iso, float* tris, long long tri_cap,
-                                  const McConst& mc, cudaStream_t st) {
+cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, const int* order, long long n_bricks,
+                                  uint4* duals, long long cap, Scratch* sc, float iso, float* tris,
+                                  long long tri_cap, const McConst& mc, cudaStream_t st) {
   if (n_bricks <= 0) return cudaSuccess;
   const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
   AMR_DISPATCH(logb, (k_dual_cells<LB, true><<<grid, DualShape<LB>::kThreads, 0, st>>>(
-                         loc, nbr, n_bricks, duals, cap, sc, iso, tris, tri_cap, mc)));
+                         loc, nbr, order, n_bricks, duals, cap, sc, iso, tris, tri_cap, mc)));
   return cudaGetLastError();
 }
 

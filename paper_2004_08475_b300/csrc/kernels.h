@@ -103,14 +103,16 @@ cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, float* s
 cudaError_t launch_brick_neighbors(int logb, Locator loc, long long n_bricks, int* nbr, int grid,
                                    cudaStream_t st);
 
-cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, long long n_bricks, uint4* duals,
-                              long long cap, Scratch* sc, cudaStream_t st);
+// order: NULL (bricks in index order) or a permutation of the bricks, the
+// order in which the CTAs visit them (see order.h).
+cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, const int* order, long long n_bricks,
+                              uint4* duals, long long cap, Scratch* sc, cudaStream_t st);
 
 // Dual cells plus Marching Cubes at `iso` on each of them in the same pass;
 // triangles appended through sc->n_tri[0] (reset by the caller).
-cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, long long n_bricks, uint4* duals,
-                                  long long cap, Scratch* sc, float iso, float* tris, long long tri_cap,
-                                  const McConst& mc, cudaStream_t st);
+cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, const int* order, long long n_bricks,
+                                  uint4* duals, long long cap, Scratch* sc, float iso, float* tris,
+                                  long long tri_cap, const McConst& mc, cudaStream_t st);
 
 cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, float iso,
                       float* tris, long long cap, unsigned long long* counter,

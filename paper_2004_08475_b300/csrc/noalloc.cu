@@ -182,7 +182,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
     NA_TRY(rc_of(launch_resolve_views(kLogB, L, view, scal, n_slots, 0, sc, grid_slots, block, st)));
     const int grid_nb = (int)std::max(1ll, std::min((n_bricks * 27 + block - 1) / block, (long long)sms * 8));
     NA_TRY(rc_of(launch_brick_neighbors(kLogB, L, n_bricks, nbr, grid_nb, st)));
-    NA_TRY(rc_of(launch_dual_cells(kLogB, L, nbr, n_bricks, duals, kMaxDuals, sc, st)));
+    NA_TRY(rc_of(launch_dual_cells(kLogB, L, nbr, nullptr, n_bricks, duals, kMaxDuals, sc, st)));
     NA_TRY(read_counters(sc, &h, st));
     NA_TRY(err_bits(h.err));
     if ((long long)h.n_occupied != n) return AMR_ERR_DUPLICATE;   // two cells shared a slot

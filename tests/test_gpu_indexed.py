@@ -132,3 +132,36 @@ def test_dual_shapes_match_oracle(seed):
     assert np.array_equal(hist, np.bincount(want, minlength=9))
     m = oracle.OracleMesh(xyz.numpy(), lv.numpy())
     assert np.array_equal(np.sort(oracle.dual_shapes(m.duals())), np.sort(want))
+
+
+def test_next_rows_on_empty_outputs():
+    """Degenerate cases: an iso-value above every scalar (no triangles), an
+    empty data set and a single cell (no duals) give empty indexed face sets,
+    empty attribute lists and an all-zero shape histogram, like the oracle."""
+    from paper_2004_08475_b300 import amriso
+    xyz, lv, s, iso, info = synth.sphere_tiny()
+    ctx = amriso.AmrContext()
+    ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+    ctx.build_locator()
+    ctx.dual_cells()
+    above = float(s.max()) + 1.0
+    for host in (False, True):
+        vtx, tri, vkeys = ctx.iso_indexed(above, host=host)
+        assert vtx.shape == (0, 3) and tri.shape == (0, 3) and vkeys.shape == (0, 2)
+    assert ctx.interpolate(above, s.cuda(), vkeys.cuda()).shape == (0,)
+    assert ctx.interpolate(above, s.clone(), vkeys.cpu()).shape == (0,)
+    m = oracle.OracleMesh(xyz.numpy(), lv.numpy())
+    r = m.iso(s.numpy(), m.duals(), above, want_keys=True)
+    assert r["tris"].shape[0] == 0 and oracle.weld(r["tris"], r["keys"])[0].shape == (0, 3)
+    for cells in (0, 1):
+        ctx.upload(torch.tensor([[4, 8, -12]][:cells], dtype=torch.int32, device="cuda").reshape(-1, 3),
+                   torch.tensor([2][:cells], dtype=torch.uint8, device="cuda"),
+                   torch.tensor([1.0][:cells], dtype=torch.float32, device="cuda"))
+        ctx.build_locator()
+        assert ctx.dual_cells() == 0
+        counts, hist = ctx.dual_shapes()
+        assert counts.shape == (0,) and not hist.any()
+        assert oracle.dual_shapes(np.zeros((0, 8), np.int64)).shape == (0,)
+        vtx, tri, vkeys = ctx.iso_indexed(0.5)
+        assert vtx.shape[0] == 0 and tri.shape[0] == 0
+    ctx.close()
