@@ -197,23 +197,77 @@ def oracle_window(xyz, lv, s, target_cells: int, seed: int = 0):
     return xyz[m], lv[m], s[m]
 
 
-def time_oracle(xyz, lv, s, iso, seconds: float = 15.0):
+def _pool_warmup(_):
+    time.sleep(0.2)
+    import oracle  # noqa: F401  (loads the oracle's library in the worker)
+    return os.getpid()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_pool(processes: int):
+    """A started spawn pool of `processes` workers for the sharded oracle, or
+    None (one process) when processes <= 1 or a pool cannot be had."""
+    if processes <= 1:
+        return None
+    try:
+        from oracle import shard
+        pool = shard.spawn_pool(processes)
+        list(pool.map(_pool_warmup, range(2 * processes)))   # workers up before any timing
+        return pool
+    except Exception as e:  # the one-process oracle is still the oracle
+        print(f"[bench] oracle process pool unavailable ({e}); timing one process", file=sys.stderr)
+        return None
+
+
+def time_oracle(xyz, lv, s, iso, seconds: float = 15.0, pool=None, processes: int = 1):
     """Oracle (cell set + duals + MC) on a window sized for about `seconds`
-    of single-thread CPU work; returns counts and the time taken."""
+    of wall time. With a pool the window is cut into `processes` x slabs of
+    equal cell counts, each with a halo of the widest cell, run side by side
+    (oracle.shard: the same duals and triangles as one process). Returns
+    counts, wall seconds, summed per-process oracle seconds and cores."""
     import oracle
-    target = 20000
+    from oracle import shard
+    par = pool is not None and processes > 1
+    target = 20000 * (processes if par else 1)
     while True:
         wx, wl, ws = oracle_window(xyz, lv, s, target)
         t0 = time.perf_counter()
-        m = oracle.OracleMesh(wx, wl)
-        d = m.duals()
-        r = m.iso(ws, d, iso, want_keys=False)
+        o = None
+        if par:
+            try:
+                o = shard.run_sharded(wx, wl, ws, iso, n_slabs=processes, executor=pool, balance="count",
+                                      want_keys=False)
+            except Exception as e:   # a broken pool: time the one-process oracle instead
+                print(f"[bench] oracle process pool failed ({e}); timing one process", file=sys.stderr)
+                par = False
+                target = max(20000, target // processes)
+                continue
+        if o is not None:
+            nd, nt, cpu_s = int(o["duals"].shape[0]), int(o["tris"].shape[0]), o["cpu_seconds"]
+        else:
+            m = oracle.OracleMesh(wx, wl)
+            d = m.duals()
+            r = m.iso(ws, d, iso, want_keys=False)
+            nd, nt, cpu_s = int(d.shape[0]), int(r["tris"].shape[0]), None
         dt = time.perf_counter() - t0
-        if dt > seconds / 4 or target > 2e7 or target >= xyz.shape[0]:
+        if dt > seconds / 4 or target > 2e7 * (processes if par else 1) or target >= xyz.shape[0]:
             break
         target = int(target * min(8.0, seconds / max(dt, 1e-3)))
-    return {"duals": int(d.shape[0]), "tris": int(r["tris"].shape[0]), "cells": int(wx.shape[0]),
-            "seconds": dt}
+    return {"duals": nd, "tris": nt, "cells": int(wx.shape[0]), "seconds": dt,
+            "cpu_seconds": dt if cpu_s is None else cpu_s, "cores": processes if par else 1}
+
+
+def oracle_sample_text(r, workload):
+    how = (f"cut into {r['cores']} x slabs (halo of the widest cell) on {r['cores']} processes"
+           if r["cores"] > 1 else "one process")
+    return (f"{r['cells']} cells in a box of the {workload} workload, {how}: {r['duals']} duals, "
+            f"{r['tris']} triangles, {r['seconds']:.1f} s wall, {r['cpu_seconds']:.1f} s oracle time summed")
 
 
 # ---------------------------------------------------------------------------
@@ -224,21 +278,25 @@ def run_reference(args, workload_desc, gen):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    cores = args.cpu_cores or host_cores()
+    pool = oracle_pool(cores)
     dev = "cuda" if (torch.cuda.is_available() and args.workload in ("wing", "block")) else "cpu"
     xyz, lv, s, iso, info = gen(dev)
     x, l, v = xyz.cpu().numpy(), lv.cpu().numpy(), s.cpu().numpy()
     per = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        time_oracle(x, l, v, iso, seconds=per)
+        time_oracle(x, l, v, iso, seconds=per, pool=pool, processes=cores)
     duals = tris = 0
     secs = 0.0
-    cells = 0
+    r = None
     for _ in range(args.steps):
-        r = time_oracle(x, l, v, iso, seconds=per)
+        r = time_oracle(x, l, v, iso, seconds=per, pool=pool, processes=cores)
         duals += r["duals"]
         tris += r["tris"]
         secs += r["seconds"]
-        cells = r["cells"]
+    if pool is not None:
+        pool.shutdown()
+    cells = r["cells"] if r else 0
     value = duals / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "dual cells/s",
@@ -248,8 +306,9 @@ def run_reference(args, workload_desc, gen):
         "config": {"workload": args.workload, "description": workload_desc, "n_cells": info["n"],
                    "sample_cells": cells},
         "triangles_per_s": tris / secs,
-        "cpu_baseline": {"value": value, "unit": "dual cells/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{cells} cells in a box of the {args.workload} workload per step"},
+        "cpu_baseline": {"value": value, "unit": "dual cells/s", "cores": r["cores"] if r else 1,
+                         "kind": "oracle", "sample": "per step: " + (oracle_sample_text(r, args.workload)
+                                                                     if r else "none")},
         "e2e": {"value": value, "unit": "dual cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -358,6 +417,9 @@ def main():
     ap.add_argument("--fused-iso", action="store_true",
                     help="amr_dual_cells_iso (one pass) instead of amr_dual_cells then amr_iso")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="processes for the CPU oracle (x slabs side by side); 0 = every core this "
+                         "process may use, 1 = the single-process oracle")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-indexed", action="store_true", help="skip the indexed face set measurement")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -588,10 +650,13 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x, l, v = xyz.cpu().numpy(), lv.cpu().numpy(), s.cpu().numpy()
-        r = time_oracle(x, l, v, iso, seconds=15.0)
-        cpu = {"value": r["duals"] / r["seconds"], "unit": "dual cells/s", "cores": 1, "kind": "oracle",
-               "sample": f"{r['cells']} cells in a box of the {args.workload} workload "
-                         f"({r['duals']} duals, {r['tris']} triangles, {r['seconds']:.1f} s)"}
+        cores = args.cpu_cores or host_cores()
+        pool = oracle_pool(cores)
+        r = time_oracle(x, l, v, iso, seconds=15.0, pool=pool, processes=cores)
+        if pool is not None:
+            pool.shutdown()
+        cpu = {"value": r["duals"] / r["seconds"], "unit": "dual cells/s", "cores": r["cores"], "kind": "oracle",
+               "sample": oracle_sample_text(r, args.workload)}
 
     if rank == 0:
         line = {

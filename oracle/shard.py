@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import multiprocessing
 import os
+import time
 from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
@@ -66,21 +67,24 @@ def slab_windows(xyz, level, n_slabs, balance="width"):
 def _one_slab(args):
     """One shard: the oracle on the window's cells, duals kept for the
     slab's owners, Marching Cubes on them. Indices are mapped back to the
-    whole data set's cell IDs."""
+    whole data set's cell IDs; "seconds" is the shard's own oracle time."""
     from oracle import OracleMesh
-    xw, lw, sw, owners_local, window, iso = args
+    xw, lw, sw, owners_local, window, iso = args[:6]
+    want_keys = args[6] if len(args) > 6 else True
+    t0 = time.perf_counter()
     m = OracleMesh(xw, lw)
     d = m.duals(owners=owners_local)
     res = {"duals": window[d] if d.shape[0] else np.zeros((0, 8), np.int64)}
     if iso is not None:
-        r = m.iso(sw, d, iso, want_keys=True)
-        res.update(cases=r["cases"], ntri=r["ntri"], tris=r["tris"],
-                   keys=window[r["keys"]] if r["keys"].shape[0] else np.zeros((0, 3, 2), np.int64),
-                   max_err=r["max_err"])
+        r = m.iso(sw, d, iso, want_keys=want_keys)
+        res.update(cases=r["cases"], ntri=r["ntri"], tris=r["tris"], max_err=r["max_err"])
+        if want_keys:
+            res["keys"] = window[r["keys"]] if r["keys"].shape[0] else np.zeros((0, 3, 2), np.int64)
+    res["seconds"] = time.perf_counter() - t0
     return res
 
 
-def shard_jobs(xyz, level, scalar, iso, n_slabs, balance="width"):
+def shard_jobs(xyz, level, scalar, iso, n_slabs, balance="width", want_keys=True):
     """The per-slab arguments of ``_one_slab`` (window arrays copied out)."""
     xyz = np.asarray(xyz, dtype=np.int32).reshape(-1, 3)
     level = np.asarray(level, dtype=np.uint8).reshape(-1)
@@ -89,29 +93,42 @@ def shard_jobs(xyz, level, scalar, iso, n_slabs, balance="width"):
     for owners, window in slab_windows(xyz, level, n_slabs, balance):
         local = np.searchsorted(window, owners)
         jobs.append((xyz[window], level[window], None if s is None else s[window], local, window,
-                     None if iso is None else float(iso)))
+                     None if iso is None else float(iso), want_keys))
     return jobs
 
 
-def run_sharded(xyz, level, scalar=None, iso=None, n_slabs=8, processes=None, balance="width"):
+def spawn_pool(processes):
+    """A process pool for ``run_sharded`` (``spawn``: safe in a process that
+    already holds a CUDA context); an executor, unlike multiprocessing.Pool,
+    raises when a worker dies instead of waiting for it."""
+    return ProcessPoolExecutor(processes, mp_context=multiprocessing.get_context("spawn"))
+
+
+def run_sharded(xyz, level, scalar=None, iso=None, n_slabs=8, processes=None, balance="width",
+                executor=None, want_keys=True):
     """Dual cells (and, given ``scalar`` and ``iso``, the Marching Cubes
     output) of the whole data set, computed slab by slab in a ``spawn``
-    process pool. Returns the concatenation over slabs, in slab order:
-    duals [D, 8] (global cell IDs), and cases, ntri, tris, keys, max_err."""
-    jobs = shard_jobs(xyz, level, scalar, iso, n_slabs, balance)
+    process pool (``executor``, or one made for the call). Returns the
+    concatenation over slabs, in slab order: duals [D, 8] (global cell IDs),
+    and cases, ntri, tris, keys, max_err; "cpu_seconds" sums the shards'
+    oracle times."""
+    jobs = shard_jobs(xyz, level, scalar, iso, n_slabs, balance, want_keys)
     processes = processes or min(n_slabs, os.cpu_count() or 1)
-    if processes <= 1:
+    if executor is not None:
+        parts = list(executor.map(_one_slab, jobs))
+    elif processes <= 1:
         parts = [_one_slab(j) for j in jobs]
     else:
-        # an executor (unlike multiprocessing.Pool) raises when a worker dies
-        with ProcessPoolExecutor(processes, mp_context=multiprocessing.get_context("spawn")) as ex:
+        with spawn_pool(processes) as ex:
             parts = list(ex.map(_one_slab, jobs))
-    out = {"duals": np.concatenate([p["duals"] for p in parts]).reshape(-1, 8)}
+    out = {"duals": np.concatenate([p["duals"] for p in parts]).reshape(-1, 8),
+           "cpu_seconds": float(sum(p["seconds"] for p in parts))}
     if iso is not None:
         out["cases"] = np.concatenate([p["cases"] for p in parts])
         out["ntri"] = np.concatenate([p["ntri"] for p in parts])
         out["tris"] = np.concatenate([p["tris"] for p in parts]).reshape(-1, 3, 3)
-        out["keys"] = np.concatenate([p["keys"] for p in parts]).reshape(-1, 3, 2)
+        if want_keys:
+            out["keys"] = np.concatenate([p["keys"] for p in parts]).reshape(-1, 3, 2)
         out["max_err"] = max([p["max_err"] for p in parts], default=0.0)
     return out
 

@@ -189,3 +189,37 @@ def test_two_gloo_ranks_sum_fingerprints():
         p.join(60)
         assert p.exitcode == 0
     assert got == want
+
+
+def test_bench_cpu_leg_on_several_processes():
+    """bench.py's CPU-baseline leg: the oracle cut into x slabs on a pool of
+    processes counts the same duals and triangles as one process."""
+    import bench
+    xyz, lv, s, iso, info = synth.random_octree(8, levels=5, roots=4, p_hole=0.08, field="sphere")
+    x, l, v = xyz.numpy(), lv.numpy(), s.numpy()
+    one = bench.time_oracle(x, l, v, iso, seconds=0.01)
+    pool = bench.oracle_pool(2)
+    assert pool is not None
+    try:
+        two = bench.time_oracle(x, l, v, iso, seconds=0.01, pool=pool, processes=2)
+    finally:
+        pool.shutdown()
+    assert one["cores"] == 1 and two["cores"] == 2
+    assert one["cells"] == two["cells"] == x.shape[0]
+    assert (one["duals"], one["tris"]) == (two["duals"], two["tris"])
+    assert "2 x slabs" in bench.oracle_sample_text(two, "random_octree")
+
+
+def test_bench_cpu_leg_survives_a_broken_pool():
+    """A pool that fails leaves the CPU leg timing the one-process oracle."""
+    import bench
+
+    class Broken:
+        def map(self, *a, **k):
+            raise RuntimeError("planted pool failure")
+
+    xyz, lv, s, iso, info = synth.random_octree(8, levels=5, roots=4, p_hole=0.08, field="sphere")
+    x, l, v = xyz.numpy(), lv.numpy(), s.numpy()
+    r = bench.time_oracle(x, l, v, iso, seconds=0.01, pool=Broken(), processes=4)
+    one = bench.time_oracle(x, l, v, iso, seconds=0.01)
+    assert r["cores"] == 1 and (r["duals"], r["tris"]) == (one["duals"], one["tris"])
