@@ -381,12 +381,13 @@ class AmrContext:
 
     def kernel_times(self):
         """{kernel name: (total ms, launches)} since the previous call."""
-        ms = (ctypes.c_double * 32)()
-        cnt = (ctypes.c_int64 * 32)()
-        k = _lib.amr_kernel_times(self._h, ms, cnt, 32)
+        cap = 64
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_int64 * cap)()
+        k = _lib.amr_kernel_times(self._h, ms, cnt, cap)
         if k < 0:
             _check(k, "amr_kernel_times")
-        return {_lib.amr_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
+        return {_lib.amr_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(min(k, cap))}
 
     def _tri_buffer(self, n, host=False):
         if host:
