@@ -60,25 +60,27 @@ def best_options(n_cells: int, levels: int, gpu: str | None = None, path: str = 
 def time_options(xyz, lvl, s, iso: float, opts: dict, reps: int = 3) -> float:
     """Median ms of upload + locator + dual cells + one iso-value."""
     ctx = amriso.AmrContext()
-    out = torch.empty((1, 3, 3), dtype=torch.float32, device="cuda")
-    ctx.upload(xyz, lvl, s)
-    ctx.build_locator(**opts)
-    ctx.dual_cells()
-    n = ctx.iso_count(iso, out)
-    out = torch.empty((max(n, 1), 3, 3), dtype=torch.float32, device="cuda")
-    times = []
-    st = torch.cuda.current_stream()
-    for _ in range(reps + 1):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
+    try:
+        out = torch.empty((1, 3, 3), dtype=torch.float32, device="cuda")
         ctx.upload(xyz, lvl, s)
         ctx.build_locator(**opts)
         ctx.dual_cells()
-        ctx.iso_count(iso, out)
-        b.record(st)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-    ctx.close()
+        n = ctx.iso_count(iso, out)
+        out = torch.empty((max(n, 1), 3, 3), dtype=torch.float32, device="cuda")
+        times = []
+        st = torch.cuda.current_stream()
+        for _ in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            ctx.upload(xyz, lvl, s)
+            ctx.build_locator(**opts)
+            ctx.dual_cells()
+            ctx.iso_count(iso, out)
+            b.record(st)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+    finally:
+        ctx.close()
     times = sorted(times[1:])
     return times[len(times) // 2]
 
@@ -99,6 +101,8 @@ def tune(xyz, lvl, s, iso: float, space: dict | None = None, reps: int = 3, path
             continue
         table.append({**opts, "ms": ms})
     ok = [r for r in table if r["ms"] is not None]
+    if not ok:
+        raise RuntimeError(f"tune: no option set could run on this data set ({table[0]['error']})")
     best = min(ok, key=lambda r: r["ms"])
     result = {"best": {k: best[k] for k in names}, "best_ms": best["ms"], "table": table}
     if path is not None:
