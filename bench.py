@@ -177,24 +177,58 @@ def reduce_over_ranks(ms: float, nd: int, nt: int, dist, device) -> tuple:
 # CPU oracle leg (bounded sample)
 # ---------------------------------------------------------------------------
 
-def oracle_window(xyz, lv, s, target_cells: int, seed: int = 0):
+def _in_box(xyz, c, half):
+    """Indices (increasing) of the rows of int32 xyz with |xyz - c| <= half on
+    every axis, one axis at a time on the surviving rows (no int64 copy of
+    the whole array)."""
+    idx = None
+    for a in range(3):
+        lo_a = max(int(np.ceil(c[a] - half[a])), -2 ** 31)
+        hi_a = min(int(np.floor(c[a] + half[a])), 2 ** 31 - 1)
+        col = xyz[:, a] if idx is None else xyz[idx, a]
+        sel = (col >= lo_a) & (col <= hi_a)
+        idx = np.flatnonzero(sel) if idx is None else idx[sel]
+    return idx
+
+
+def oracle_window(xyz, lv, s, target_cells: int, seed: int = 0, sub_max: int = 4_000_000):
     """Cells inside a box around a finest-level cell holding about
-    `target_cells` cells (numpy arrays in, numpy arrays out)."""
-    x = xyz.astype(np.int64)
-    lo, hi = x.min(0), x.max(0) + 1
-    fine = np.where(lv == lv.min())[0]
+    `target_cells` cells (numpy arrays in, numpy arrays out, input order).
+    The box is sized on a random subsample of at most `sub_max` cells, then
+    cut from all cells in one pass (corrected if the estimate missed)."""
+    n = xyz.shape[0]
+    if n == 0:
+        return xyz, lv, s
+    lo, hi = xyz.min(0).astype(np.int64), xyz.max(0).astype(np.int64) + 1
     rng = np.random.default_rng(seed)
-    c = x[fine[rng.integers(0, fine.shape[0])]] if fine.size else (lo + hi) // 2
-    frac = min(1.0, target_cells / max(1, x.shape[0]))
-    half = np.maximum((hi - lo) * frac ** (1 / 3) / 2, 1)
-    m = np.ones(x.shape[0], dtype=bool)
-    for _ in range(40):
-        m = (np.abs(x - c) <= half).all(1)
-        k = int(m.sum())
-        if 0.8 * target_cells <= k <= 1.25 * target_cells or k == x.shape[0]:
+    lmin = lv.min()
+    c = None
+    for _ in range(1000):            # a random finest-level cell (rejection sampling)
+        i = int(rng.integers(0, n))
+        if lv[i] == lmin:
+            c = xyz[i].astype(np.int64)
             break
-        half = half * (target_cells / max(k, 1)) ** (1 / 3)
-    return xyz[m], lv[m], s[m]
+    if c is None:
+        fine = np.flatnonzero(lv == lmin)
+        c = xyz[fine[rng.integers(0, fine.shape[0])]].astype(np.int64)
+    t = float(target_cells)
+    half = np.maximum((hi - lo) * min(1.0, t / n) ** (1 / 3) / 2, 1)
+    if n > sub_max:
+        xs = xyz[np.unique(rng.integers(0, n, size=sub_max))]
+        f = xs.shape[0] / n
+        for _ in range(40):
+            k = _in_box(xs, c, half).shape[0] / f
+            if 0.8 * t <= k <= 1.25 * t:
+                break
+            half = half * (t / max(k, 1.0)) ** (1 / 3)
+    idx = _in_box(xyz, c, half)
+    for _ in range(40):
+        k = int(idx.shape[0])
+        if 0.8 * t <= k <= 1.25 * t or k == n:
+            break
+        half = half * (t / max(k, 1)) ** (1 / 3)
+        idx = _in_box(xyz, c, half)
+    return xyz[idx], lv[idx], s[idx]
 
 
 def _pool_warmup(_):
@@ -225,42 +259,55 @@ def oracle_pool(processes: int):
         return None
 
 
-def time_oracle(xyz, lv, s, iso, seconds: float = 15.0, pool=None, processes: int = 1):
-    """Oracle (cell set + duals + MC) on a window sized for about `seconds`
-    of wall time. With a pool the window is cut into `processes` x slabs of
-    equal cell counts, each with a halo of the widest cell, run side by side
+def run_oracle_once(wx, wl, ws, iso, pool=None, processes: int = 1):
+    """One run of the oracle (cell set + duals + MC) over a sample of cells.
+    With a pool the sample is cut into `processes` x slabs of equal cell
+    counts, each with a halo of the widest cell, run side by side
     (oracle.shard: the same duals and triangles as one process). Returns
-    counts, wall seconds, summed per-process oracle seconds and cores."""
+    counts, wall seconds, summed per-process oracle seconds and cores; a pool
+    failure raises."""
     import oracle
     from oracle import shard
+    t0 = time.perf_counter()
+    if pool is not None and processes > 1:
+        o = shard.run_sharded(wx, wl, ws, iso, n_slabs=processes, executor=pool, balance="count",
+                              want_keys=False)
+        nd, nt, cpu_s, cores = int(o["duals"].shape[0]), int(o["tris"].shape[0]), o["cpu_seconds"], processes
+    else:
+        m = oracle.OracleMesh(wx, wl)
+        d = m.duals()
+        r = m.iso(ws, d, iso, want_keys=False)
+        nd, nt, cpu_s, cores = int(d.shape[0]), int(r["tris"].shape[0]), None, 1
+    dt = time.perf_counter() - t0
+    return {"duals": nd, "tris": nt, "cells": int(wx.shape[0]), "seconds": dt,
+            "cpu_seconds": dt if cpu_s is None else cpu_s, "cores": cores}
+
+
+def time_oracle(xyz, lv, s, iso, seconds: float = 15.0, pool=None, processes: int = 1):
+    """The oracle on a box of cells grown until one run takes about
+    `seconds` / 4 to `seconds` of wall time (on `processes` processes when a
+    pool is given); returns the last run (run_oracle_once) plus "window",
+    the sample, for further timed runs. A pool that fails is dropped and
+    the one-process oracle timed instead ("pool": the pool still in use)."""
     par = pool is not None and processes > 1
     target = 20000 * (processes if par else 1)
     while True:
-        wx, wl, ws = oracle_window(xyz, lv, s, target)
-        t0 = time.perf_counter()
-        o = None
-        if par:
-            try:
-                o = shard.run_sharded(wx, wl, ws, iso, n_slabs=processes, executor=pool, balance="count",
-                                      want_keys=False)
-            except Exception as e:   # a broken pool: time the one-process oracle instead
-                print(f"[bench] oracle process pool failed ({e}); timing one process", file=sys.stderr)
-                par = False
-                target = max(20000, target // processes)
-                continue
-        if o is not None:
-            nd, nt, cpu_s = int(o["duals"].shape[0]), int(o["tris"].shape[0]), o["cpu_seconds"]
-        else:
-            m = oracle.OracleMesh(wx, wl)
-            d = m.duals()
-            r = m.iso(ws, d, iso, want_keys=False)
-            nd, nt, cpu_s = int(d.shape[0]), int(r["tris"].shape[0]), None
-        dt = time.perf_counter() - t0
-        if dt > seconds / 4 or target > 2e7 * (processes if par else 1) or target >= xyz.shape[0]:
+        win = oracle_window(xyz, lv, s, target)
+        try:
+            r = run_oracle_once(*win, iso, pool if par else None, processes if par else 1)
+        except Exception as e:   # a broken pool: time the one-process oracle instead
+            if not par:
+                raise
+            print(f"[bench] oracle process pool failed ({e}); timing one process", file=sys.stderr)
+            par = False
+            target = max(20000, target // processes)
+            continue
+        if r["seconds"] > seconds / 4 or target > 2e7 * (processes if par else 1) or target >= xyz.shape[0]:
             break
-        target = int(target * min(8.0, seconds / max(dt, 1e-3)))
-    return {"duals": nd, "tris": nt, "cells": int(wx.shape[0]), "seconds": dt,
-            "cpu_seconds": dt if cpu_s is None else cpu_s, "cores": processes if par else 1}
+        target = int(target * min(8.0, seconds / max(r["seconds"], 1e-3)))
+    r["window"] = win
+    r["pool"] = pool if par else None
+    return r
 
 
 def oracle_sample_text(r, workload):
@@ -283,20 +330,32 @@ def run_reference(args, workload_desc, gen):
     dev = "cuda" if (torch.cuda.is_available() and args.workload in ("wing", "block")) else "cpu"
     xyz, lv, s, iso, info = gen(dev)
     x, l, v = xyz.cpu().numpy(), lv.cpu().numpy(), s.cpu().numpy()
+    # one sample of the workload sized once (untimed), then every step runs it
     per = max(1.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        time_oracle(x, l, v, iso, seconds=per, pool=pool, processes=cores)
-    duals = tris = 0
-    secs = 0.0
-    r = None
-    for _ in range(args.steps):
-        r = time_oracle(x, l, v, iso, seconds=per, pool=pool, processes=cores)
-        duals += r["duals"]
-        tris += r["tris"]
-        secs += r["seconds"]
+    use = pool
+    while True:
+        cal = time_oracle(x, l, v, iso, seconds=per, pool=use, processes=cores)
+        win, use = cal["window"], cal["pool"]
+        try:
+            for _ in range(args.warmup):
+                run_oracle_once(*win, iso, use, cores)
+            duals = tris = 0
+            secs = 0.0
+            r = cal
+            for _ in range(args.steps):
+                r = run_oracle_once(*win, iso, use, cores)
+                duals += r["duals"]
+                tris += r["tris"]
+                secs += r["seconds"]
+            break
+        except Exception as e:   # the pool broke after sizing: size and time one process
+            if use is None:
+                raise
+            print(f"[bench] oracle process pool failed ({e}); timing one process", file=sys.stderr)
+            use = None
     if pool is not None:
         pool.shutdown()
-    cells = r["cells"] if r else 0
+    cells = r["cells"]
     value = duals / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "dual cells/s",
@@ -306,9 +365,8 @@ def run_reference(args, workload_desc, gen):
         "config": {"workload": args.workload, "description": workload_desc, "n_cells": info["n"],
                    "sample_cells": cells},
         "triangles_per_s": tris / secs,
-        "cpu_baseline": {"value": value, "unit": "dual cells/s", "cores": r["cores"] if r else 1,
-                         "kind": "oracle", "sample": "per step: " + (oracle_sample_text(r, args.workload)
-                                                                     if r else "none")},
+        "cpu_baseline": {"value": value, "unit": "dual cells/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": "per step, the same sample: " + oracle_sample_text(r, args.workload)},
         "e2e": {"value": value, "unit": "dual cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -223,3 +223,24 @@ def test_bench_cpu_leg_survives_a_broken_pool():
     r = bench.time_oracle(x, l, v, iso, seconds=0.01, pool=Broken(), processes=4)
     one = bench.time_oracle(x, l, v, iso, seconds=0.01)
     assert r["cores"] == 1 and (r["duals"], r["tris"]) == (one["duals"], one["tris"])
+
+
+def test_bench_oracle_window_is_a_box():
+    """bench.py's sample: exactly the cells within a box around a finest-level
+    cell (brute force over all cells), about the requested size, in input
+    order."""
+    import bench
+    xyz, lv, s, iso, info = synth.octree_gaussians(seed=12, roots=4, root_level=4)
+    x, l, v = xyz.numpy(), lv.numpy(), s.numpy()
+    for target, sub_max in ((500, 1 << 30), (5000, 1 << 30), (50000, 1 << 30), (5000, 40000), (50000, 40000)):
+        wx, wl, ws = bench.oracle_window(x, l, v, target, seed=3, sub_max=sub_max)
+        # (the box grows in whole cell layers, so small targets land within a factor 2)
+        assert 0.4 * target <= wx.shape[0] <= 2.5 * target
+        # the box: the tightest box around the window, centred on a finest cell
+        lo, hi = wx.min(0).astype(np.int64), wx.max(0).astype(np.int64)
+        inside = np.all((x >= lo) & (x <= hi), axis=1)
+        assert inside.sum() == wx.shape[0]
+        assert np.array_equal(x[inside], wx) and np.array_equal(l[inside], wl) and np.array_equal(v[inside], ws)
+        assert (wl == l.min()).any()
+    empty = bench.oracle_window(x[:0], l[:0], v[:0], 100)
+    assert empty[0].shape == (0, 3)
