@@ -199,8 +199,10 @@ def oracle_window(xyz, lv, s, target_cells: int, seed: int = 0, sub_max: int = 4
     n = xyz.shape[0]
     if n == 0:
         return xyz, lv, s
-    lo, hi = xyz.min(0).astype(np.int64), xyz.max(0).astype(np.int64) + 1
     rng = np.random.default_rng(seed)
+    # drawn with replacement: count / f estimates the box's cell count
+    xs = xyz[rng.integers(0, n, size=sub_max)] if n > sub_max else xyz
+    lo, hi = xs.min(0).astype(np.int64), xs.max(0).astype(np.int64) + 1
     lmin = lv.min()
     c = None
     for _ in range(1000):            # a random finest-level cell (rejection sampling)
@@ -214,7 +216,6 @@ def oracle_window(xyz, lv, s, target_cells: int, seed: int = 0, sub_max: int = 4
     t = float(target_cells)
     half = np.maximum((hi - lo) * min(1.0, t / n) ** (1 / 3) / 2, 1)
     if n > sub_max:
-        xs = xyz[np.unique(rng.integers(0, n, size=sub_max))]
         f = xs.shape[0] / n
         for _ in range(40):
             k = _in_box(xs, c, half).shape[0] / f
