@@ -35,14 +35,19 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
+# A variant build of oracle.cpp to load instead (tests/test_oracle_mutants.py
+# runs the pins against copies with planted mistakes this way).
+_VARIANT = os.environ.get("AMR_ORACLE_VARIANT_LIB")
+
+COMPILE = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
 
 
 def build(force: bool = False) -> str:
     """Compile oracle.cpp into liboracle.so (g++, no FMA contraction)."""
+    if _VARIANT:
+        return _VARIANT
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
-               "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC]
-        subprocess.check_call(cmd)
+        subprocess.check_call(COMPILE + ["-o", _LIB + ".tmp", _SRC])
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
 
