@@ -93,6 +93,17 @@ def test_case_face_rule(case):
             directed.add(d)
 
 
+def test_no_triangle_lies_in_a_cube_face():
+    """Face rule, last clause: no triangle of any case has its three vertices
+    on one face of the cube (a neighbouring dual shares that face, and a flat
+    triangle there would fold the surface into the face)."""
+    for case in range(256):
+        for t in oracle.case_triangles(case):
+            common = set(_faces_of_edge(int(t[0]))) & set(_faces_of_edge(int(t[1]))) & \
+                set(_faces_of_edge(int(t[2])))
+            assert not common, (case, t.tolist())
+
+
 def test_case_count_histogram():
     """Up to 5 triangles per case (Sec. 5.2); cases 0 and 255 are empty."""
     counts = [oracle.case_triangles(c).shape[0] for c in range(256)]

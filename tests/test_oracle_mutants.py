@@ -4,8 +4,8 @@ Each mutant is a copy of oracle/oracle.cpp with one planted mistake (a
 dropped rejection rule or a non-strict rule-3 order, the other dual offsets,
 an unmasked snap query, a wrong sign or a transposed operand in the vertex
 formula, a dropped half in the cell centre, the ambiguous-face pairing
-around outside corners, the degenerate-triangle drop removed, ties counted
-as inside). The oracle pin
+around outside corners, loops fanned from their first edge, the
+degenerate-triangle drop removed, ties counted as inside). The oracle pin
 suites (test_oracle_duals.py, test_oracle_mc.py) run against each mutant in a
 child process and must fail with an assertion (or crash partway); against
 an unmodified copy they must pass. CPU only.
@@ -53,9 +53,7 @@ MUTANTS = {
             pr[np][0] = (r + 3) % 4;""", """        for (int r = 0; r < 4; ++r)
           if (!inside[ring[r]]) {
             pr[np][0] = (r + 3) % 4;""")],
-    # (fanning each loop from its smallest edge index instead of the first
-    # apex whose diagonals leave the cube faces is the other reading of the
-    # face walk: the same vertices and a crack-free surface, so no pin sees it)
+    "fan_apex_first": [("    int apex = -1;\n    for (int cand", "    int apex = 0;\n    for (int cand")],
     "degenerate_kept": [("if (same(vt[0], vt[1]) || same(vt[1], vt[2]) || same(vt[0], vt[2]))\n        continue;",
                          "if (false)\n        continue;")],
     "ties_inside": [("if (s[v[e]] > iso) cas |= 1 << e;", "if (s[v[e]] >= iso) cas |= 1 << e;")],
