@@ -8,7 +8,10 @@ around outside corners, loops fanned from their first edge, the
 degenerate-triangle drop removed, ties counted as inside). The oracle pin
 suites (test_oracle_duals.py, test_oracle_mc.py) run against each mutant in a
 child process and must fail with an assertion (or crash partway); against
-an unmodified copy they must pass. CPU only.
+an unmodified copy they must pass. The oracle's Python functions (weld,
+interpolate, dual_shapes, the sharded oracle) get the same treatment
+in-process: a mutated copy is patched in and one of their pins must fail.
+CPU only.
 """
 import os
 import subprocess
@@ -105,3 +108,74 @@ def test_mutant_fails_a_pin(results, name):
         return
     assert rc == 1, out[-3000:]                    # 1: tests failed (not a usage or collection error)
     assert "failed" in out and ("AssertionError" in out or "assert" in out), out[-3000:]
+
+
+# ---- the oracle's Python functions: mutants planted in-process -------------
+
+def _mutated(fn, edits):
+    """`fn` recompiled from its source with the textual edits applied, in the
+    namespace of its module."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(fn))
+    for old, new in edits:
+        assert src.count(old) == 1, (fn.__name__, old)
+        src = src.replace(old, new)
+    ns = dict(fn.__globals__)
+    exec(compile(src, f"<mutant of {fn.__name__}>", "exec"), ns)
+    return ns[fn.__name__]
+
+
+def _pins():
+    from tests import test_oracle_duals as duals_pins
+    from tests import test_oracle_mc as mc_pins
+    from tests import test_oracle_shard as shard_pins
+    return {
+        "interpolate": [mc_pins.test_interpolate_closed_forms],
+        "weld": [mc_pins.test_weld_sphere_indexed_face_set, mc_pins.test_weld_rejects_two_positions_for_one_key],
+        "dual_shapes": [duals_pins.test_dual_shapes_pins],
+        "shard": [lambda: shard_pins.test_sharded_equals_unsharded(*shard_pins.CASES[0])],
+    }
+
+
+PY_MUTANTS = {
+    "interpolate_higher_first": ("interpolate", [("tuple(q) < tuple(p)", "tuple(q) > tuple(p)")]),
+    "interpolate_t_sign": ("interpolate", [("t = (iso32 - s[a]) / (s[b] - s[a])", "t = (s[a] - iso32) / (s[b] - s[a])")]),
+    "interpolate_from_b": ("interpolate", [("f[a] + t * (f[b] - f[a])", "f[b] + t * (f[a] - f[b])")]),
+    "weld_unchecked": ("weld", [("if not np.array_equal(vtx[inv.reshape(-1)].view(np.int32), p.view(np.int32)):",
+                                 "if False:")]),
+    "weld_wrong_index": ("weld", [("return vtx, inv.reshape(-1, 3).astype(np.int64), vkeys",
+                                   "return vtx, np.sort(inv.reshape(-1, 3), axis=1).astype(np.int64), vkeys")]),
+    "dual_shapes_off_by_one": ("dual_shapes", [("return (1 + (d[:, 1:] != d[:, :-1]).sum(axis=1))",
+                                                "return ((d[:, 1:] != d[:, :-1]).sum(axis=1))")]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_python_mutant_fails_a_pin(monkeypatch, name):
+    fn_name, edits = PY_MUTANTS[name]
+    mutant = _mutated(getattr(oracle, fn_name), edits)
+    monkeypatch.setattr(oracle, fn_name, mutant)
+    caught = False
+    for pin in _pins()[fn_name]:
+        try:
+            pin()
+        except (AssertionError, oracle.OracleError, pytest.fail.Exception):   # a failed pin
+            caught = True
+    assert caught, name
+
+
+def test_python_pins_pass_unmodified():
+    for pins in _pins().values():
+        for pin in pins:
+            pin()
+
+
+def test_shard_without_owner_filter_fails_a_pin(monkeypatch):
+    """The sharded oracle keeping every dual its window emits (halo owners
+    included) instead of the slab's own: duplicates and wrong duals."""
+    from oracle import shard
+    mutant = _mutated(shard._one_slab, [("d = m.duals(owners=owners_local)", "d = m.duals()")])
+    monkeypatch.setattr(shard, "_one_slab", mutant)
+    with pytest.raises(AssertionError):
+        _pins()["shard"][0]()
