@@ -81,6 +81,28 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int, place
     }.get(kernel, 0.0)
 
 
+def paper_bytes(stage: str, n: int, nd: int, nt: int) -> float:
+    """The method's irreducible bytes per stage (the scope table's byte
+    model, independent of this implementation's layout): locator 13 B per
+    cell read (corner, level) + 12 B written (key, ID); dual pass 13 + 12 B
+    per cell + 32 B per dual; Marching Cubes 32 B per dual + 17 B per cell
+    (corner, level, scalar once) + 36 B per triangle. Staging passes, table
+    slack and re-reads are implementation overhead and not counted."""
+    return {
+        "locator": 25.0 * n,
+        "dual": 25.0 * n + 32.0 * nd,
+        "mc": 32.0 * nd + 17.0 * n + 36.0 * nt,
+        "step": 67.0 * n + 64.0 * nd + 36.0 * nt,
+    }[stage]
+
+
+# kernels whose work is exactly one stage of the method
+PAPER_STAGE = {"k_mc": "mc", "k_dual_cells": "dual"}
+LOCATOR_KERNELS = ("k_insert_bricks", "k_insert_bin", "k_scatter_cells", "k_bin_coarse", "k_bin_fine",
+                   "k_place_windows", "k_resolve_views", "k_resolve_empty", "k_brick_neighbors",
+                   "k_order_count", "k_order_scan", "k_order_scatter")
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -559,9 +581,7 @@ def main():
         nd_all, nt_all = float(nd), float(nt)
 
     kt = {k: v for k, v in ktimes.items() if v[1] > 0}
-    t_loc = sum(kt.get(k, (0, 0))[0] for k in ("k_insert_bricks", "k_scatter_cells", "k_bin_coarse", "k_bin_fine",
-                                               "k_place_windows", "k_resolve_views", "k_brick_neighbors",
-                                               "k_order_count", "k_order_scan", "k_order_scatter")) / args.steps
+    t_loc = sum(kt.get(k, (0, 0))[0] for k in LOCATOR_KERNELS) / args.steps
     t_dual = (kt.get("k_dual_cells", (0, 1))[0] + kt.get("k_dual_cells_iso", (0, 1))[0]) / args.steps
     t_iso = kt.get("k_mc", (0, 1))[0] / args.steps
     launches = int(sum(v[1] for v in kt.values()))
@@ -575,26 +595,37 @@ def main():
         b = algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement, inf.log2_brick)
         kernels[k] = {"ms_per_launch": per, "launches": cnt, "share": tot_ms / total_kms,
                       "algorithmic_bytes": b, "gbs": b / per / 1e6 if per > 0 else 0.0}
-    dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
+    for k, rec in kernels.items():
+        if k in PAPER_STAGE:
+            pb = paper_bytes(PAPER_STAGE[k], n, nd, nt)
+            rec["paper_bytes"] = pb
+            rec["paper_gbs"] = pb / rec["ms_per_launch"] / 1e6 if rec["ms_per_launch"] > 0 else 0.0
+    # the dominant kernel among those that are one stage of the method each
+    # (the locator's stage spans several kernels: reported under "rates")
+    staged = [k for k in kernels if k in PAPER_STAGE] or list(kernels)
+    dom = max(staged, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
     dk = kernels[dom]
-    units = {"k_insert_bricks": n, "k_scatter_cells": n, "k_bin_coarse": n, "k_bin_fine": n,
+    units = {"k_insert_bricks": n, "k_insert_bin": n, "k_scatter_cells": n, "k_bin_coarse": n, "k_bin_fine": n,
              "k_place_windows": inf.n_slots, "k_resolve_views": inf.n_slots,
              "k_dual_cells": inf.n_slots, "k_dual_cells_iso": inf.n_slots, "k_mc": nd}.get(dom, n)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": dk["gbs"] / peak, "peak_source": peak_src,
+    ach = dk.get("paper_gbs", dk["gbs"])
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_src,
                 "traffic": ncu_traffic(dom, args.workload, units),
-                "algorithmic_bytes_per_launch": dk["algorithmic_bytes"]}
-    step_bytes = sum(algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement, inf.log2_brick) * v[1]
-                     for k, v in kt.items()) / args.steps
+                "algorithmic_bytes_per_launch": dk.get("paper_bytes", dk["algorithmic_bytes"]),
+                "bytes_model": "method (32 B/dual + 17 B/cell + 36 B/triangle for k_mc; 25 B/cell + 32 B/dual "
+                               "for k_dual_cells)" if dom in PAPER_STAGE else "implementation",
+                "impl_model_bytes_per_launch": dk["algorithmic_bytes"],
+                "frac_impl_model": dk["gbs"] / peak}
+    step_bytes_impl = sum(algorithmic_bytes(k, n, inf.n_slots, nd, nt, inf.placement, inf.log2_brick) * v[1]
+                          for k, v in kt.items()) / args.steps
+    step_bytes = paper_bytes("step", n, nd, nt)
 
     # batched multi-iso over the resident dual cells
     batch = None
     if args.batch_isos > 0 and rank == 0:
-        srt = torch.sort(s).values
-        lo_q, hi_q = 0.40, 0.95
-        isos = [float(srt[int((lo_q + (hi_q - lo_q) * k / max(1, args.batch_isos - 1)) * (n - 1))])
-                for k in range(args.batch_isos)]
-        del srt
+        # the workload's iso-value times 2^((k-8)/4), k = 0..15: quarter-octave steps around it
+        isos = [float(iso * 2.0 ** ((k - args.batch_isos // 2) / 4)) for k in range(args.batch_isos)]
         _, offs = ctx.iso_batch(isos, torch.empty((0, 3, 3), dtype=torch.float32, device="cuda"))
         need = int(offs[-1])
         torch.cuda.empty_cache()
@@ -613,9 +644,11 @@ def main():
         bt = ctx.kernel_times()
         ctx.enable_timing(False)
         bms = e0.elapsed_time(e1) / reps
-        batch = {"n_iso": len(isos), "iso_quantiles": [lo_q, hi_q], "ms": bms, "triangles": need,
+        bb = 32.0 * nd + 17.0 * n + 36.0 * need   # method bytes of k iso-values batched
+        batch = {"n_iso": len(isos), "isos": "iso * 2^((k-8)/4), k = 0..15", "ms": bms, "triangles": need,
                  "triangles_per_s": need / (bms / 1e3), "ms_per_iso": bms / len(isos),
-                 "single_iso_kernel_ms": t_iso,
+                 "single_iso_kernel_ms": t_iso, "paper_bytes": bb,
+                 "frac_of_peak": bb / (bms / 1e3) / 1e9 / peak,
                  "kernels_ms": {k: v[0] / reps for k, v in bt.items() if v[1]}}
         del buf
         torch.cuda.empty_cache()
@@ -735,8 +768,14 @@ def main():
             "triangles_per_s": nt_all / (ms / 1e3),
             "rates": {"dual_cells_per_s_locator_plus_dual": nd / ((t_loc + t_dual) / 1e3) if t_loc + t_dual else None,
                       "triangles_per_s_iso_kernel": nt / (t_iso / 1e3) if t_iso else None,
+                      "step_bytes": step_bytes,
                       "step_algorithmic_gbs": step_bytes / (ms / 1e3) / 1e9,
-                      "step_frac_of_peak": step_bytes / (ms / 1e3) / 1e9 / peak},
+                      "step_frac_of_peak": step_bytes / (ms / 1e3) / 1e9 / peak,
+                      "locator_ms": t_loc, "dual_ms": t_dual, "mc_ms": t_iso,
+                      "locator_frac_of_peak": (paper_bytes("locator", n, nd, nt) / (t_loc / 1e3) / 1e9 / peak
+                                               if t_loc else None),
+                      "step_bytes_impl_model": step_bytes_impl,
+                      "step_frac_impl_model": step_bytes_impl / (ms / 1e3) / 1e9 / peak},
             "roofline": roofline,
             "kernels": kernels,
             "batched_iso": batch,

@@ -148,6 +148,20 @@ int amr_get_duals(amr_ctx* ctx, int32_t* out, int64_t cap, int flags);
 int amr_iso(amr_ctx* ctx, float iso, float* tris, int64_t cap, int64_t* n_tris,
             int flags);
 
+/* amr_iso with, beside every triangle written, the index of the dual cell
+ * that produced it: the triangle -> dual map that lets a reader check the
+ * triangles of each dual cell on its own (Sec. 5 extracts each dual's
+ * triangles independently of every other dual's).
+ *   tris     [cap][3][3] fp32, as amr_iso (the same triangles, same order
+ *            rules);
+ *   tri_dual [cap] int64: row t of tris came from dual tri_dual[t], an
+ *            index into the resident list (the order of amr_get_duals and
+ *            amr_iso_cases).
+ * Both arrays are device memory, or host memory with AMR_HOST_PTRS. *n_tris
+ * and AMR_ERR_CAPACITY as amr_iso. Synchronises the stream. */
+int amr_iso_tagged(amr_ctx* ctx, float iso, float* tris, int64_t* tri_dual, int64_t cap,
+                   int64_t* n_tris, int flags);
+
 /* Indexed face set of the same surface (the indexed output the paper builds
  * after its extraction, Sec. 5.2, with vertices welded by their integer edge
  * key - the unordered pair of cells a vertex interpolates between - instead
@@ -240,7 +254,7 @@ const char* amr_strerror(int code);
  * of the build); a binding compares it with the header it was written for
  * and refuses a library built from other sources. No counterpart in the
  * paper. */
-#define AMR_ABI_VERSION 8
+#define AMR_ABI_VERSION 9
 int amr_abi_version(void);
 
 /* ---- introspection (host only, no device needed) ------------------------ */

@@ -62,7 +62,7 @@ class _Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("placement", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-ABI_VERSION = 8   # AMR_ABI_VERSION of include/amriso.h
+ABI_VERSION = 9   # AMR_ABI_VERSION of include/amriso.h
 
 
 def _load() -> ctypes.CDLL:
@@ -81,6 +81,7 @@ def _load() -> ctypes.CDLL:
         "amr_get_duals": (I, [P, P, I64, I]),
         "amr_dual_cells_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), I]),
         "amr_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), I]),
+        "amr_iso_tagged": (I, [P, F, P, P, I64, ctypes.POINTER(I64), I]),
         "amr_iso_indexed": (I, [P, F, P, I64, P, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64), I]),
         "amr_interpolate": (I, [P, F, P, P, I64, P, I]),
         "amr_dual_shapes": (I, [P, P, P, I]),
@@ -116,7 +117,7 @@ EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_bui
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
            "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async",
            "amr_dual_cells_iso", "amr_trim", "amr_abi_version", "amr_iso_indexed",
-           "amr_interpolate", "amr_dual_shapes")
+           "amr_interpolate", "amr_dual_shapes", "amr_iso_tagged")
 
 
 def lib() -> ctypes.CDLL:
@@ -266,6 +267,25 @@ class AmrContext:
                               ctypes.byref(n), flags)
         _check(rc, "amr_iso")
         return out[:n.value]
+
+    def iso_tagged(self, iso: float, host: bool = False):
+        """(tris fp32 [T,3,3], tri_dual int64 [T]): the triangles of `iso`,
+        each with the index of its dual cell in get_duals order."""
+        n = ctypes.c_int64(0)
+        flags = HOST_PTRS if host else DEVICE_PTRS
+        cap = max(1024, self.n_dual // 4)
+        for _ in range(2):
+            tris = self._tri_buffer(cap, host)
+            tags = torch.empty(cap, dtype=torch.int64, device="cpu" if host else self.device)
+            if host:
+                tags = tags.pin_memory()
+            rc = _lib.amr_iso_tagged(self._h, ctypes.c_float(iso), _ptr(tris), _ptr(tags), int(cap),
+                                     ctypes.byref(n), flags)
+            if rc != ERR_CAPACITY:
+                break
+            cap = n.value
+        _check(rc, "amr_iso_tagged")
+        return tris[:n.value], tags[:n.value]
 
     def iso_indexed(self, iso: float, host: bool = False, with_keys: bool = True):
         """Indexed face set at `iso`: (vtx [V,3] f32, tri [T,3] i32, keys [V,2]

@@ -31,13 +31,15 @@ struct DevBuf {
 enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
   KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_BIN_FINE, KT_MC_KEYS, KT_WELD_INSERT,
-  KT_WELD_INDEX, KT_INTERPOLATE, KT_SHAPES, KT_ORDER_COUNT, KT_ORDER_SCAN, KT_ORDER_SCATTER, KT_COUNT
+  KT_WELD_INDEX, KT_INTERPOLATE, KT_SHAPES, KT_ORDER_COUNT, KT_ORDER_SCAN, KT_ORDER_SCATTER, KT_MC_TAGGED,
+  KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
     "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
     "k_bin_coarse", "k_place_windows", "k_dual_cells_iso", "k_bin_fine", "k_mc_keys", "k_weld_insert",
-    "k_weld_index", "k_interpolate", "k_dual_shapes", "k_order_count", "k_order_scan", "k_order_scatter"};
+    "k_weld_index", "k_interpolate", "k_dual_shapes", "k_order_count", "k_order_scan", "k_order_scatter",
+    "k_mc_tagged"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -643,6 +645,44 @@ int amr_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t* n_tris, in
   *n_tris = nt;
   if (flags & AMR_HOST_PTRS) {
     AMR_TRY(deliver(c, tris, dst, (size_t)std::min<long long>(nt, cap) * 36, flags));
+    AMR_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return nt > cap ? AMR_ERR_CAPACITY : AMR_OK;
+}
+
+int amr_iso_tagged(amr_ctx* c, float iso, float* tris, int64_t* tri_dual, int64_t cap, int64_t* n_tris,
+                   int flags) {
+  if (!c || !n_tris || cap < 0 || (cap > 0 && (!tris || !tri_dual))) return AMR_ERR_INVALID_ARG;
+  if (c->stage < 3) return AMR_ERR_STATE;
+  AMR_CUDA(cudaSetDevice(c->device));
+  float* dst = tris;
+  long long* dtag = reinterpret_cast<long long*>(tri_dual);
+  const bool host = (flags & AMR_HOST_PTRS) != 0;
+  if (host && cap > 0) {
+    AMR_TRY(ensure(c->stage_buf, (size_t)cap * 44));
+    dst = static_cast<float*>(c->stage_buf.p);
+    dtag = reinterpret_cast<long long*>(static_cast<unsigned char*>(c->stage_buf.p) + (size_t)cap * 36);
+  }
+  unsigned long long* counter = &dev_sc(c)->n_tri[0];
+  AMR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), c->stream));
+  if (cap > 0) {   // without an output there is nothing to tag: count only
+    KernelTimer kt(c, KT_MC_TAGGED);
+    AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), c->n_dual, iso, dst, cap,
+                       counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream, dtag));
+  } else {
+    KernelTimer kt(c, KT_MC);
+    AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), c->n_dual, iso, nullptr,
+                       0, counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream));
+  }
+  AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], counter, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  const long long nt = (long long)c->host_sc->n_tri[0];
+  *n_tris = nt;
+  if (host && cap > 0) {
+    const size_t w = (size_t)std::min<long long>(nt, cap);
+    AMR_TRY(deliver(c, tris, dst, w * 36, flags));
+    AMR_TRY(deliver(c, tri_dual, dtag, w * 8, flags));
     AMR_CUDA(cudaStreamSynchronize(c->stream));
   }
   return nt > cap ? AMR_ERR_CAPACITY : AMR_OK;

@@ -1200,11 +1200,14 @@ __device__ __forceinline__ unsigned long long slot_pair(unsigned a, unsigned b) 
 
 // KEYS: instead of vertex positions, each triangle's 3 edge keys (u64) go to
 // tris reinterpreted as [cap][3] u64 (for the indexed face set).
-template <int LOGB, bool EMIT, bool CASES, bool KEYS = false>
+// TAG: besides each triangle, tags[row] = the index of its dual cell in the
+// list (what lets a reader check the triangles dual by dual).
+template <int LOGB, bool EMIT, bool CASES, bool KEYS = false, bool TAG = false>
 __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restrict__ duals, long long nd,
                                             float iso, float* __restrict__ tris, long long cap,
                                             unsigned long long* counter, unsigned char* cases,
-                                            unsigned char* ntri, const __grid_constant__ McConst mc) {
+                                            unsigned char* ntri, long long* __restrict__ tags,
+                                            const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
   extern __shared__ __align__(16) unsigned mc_smem[];
   load_mc(sh, mc);
@@ -1287,6 +1290,8 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
         } else {
           const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
           for (long long k = lane; k < lim; k += 32) tris[9 * first + k] = wst[k];
+          if (TAG)
+            for (long long k = lane; k < lim / 9; k += 32) tags[first + k] = base + (long long)(list[k] & 0xFFu);
         }
         __syncwarp();
       } else if (KEYS) {   // more triangles than the stage holds: each lane writes its own keys
@@ -1315,6 +1320,9 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
 #pragma unroll
           for (int e = 0; e < 8; ++e) q0[e] = s0[e];
           write_triangles<LOGB>(L.bricks, r0, q0, iso, sh.packed[c0], k0, idx, cap, tris, mc.edge_a, mc.edge_b);
+          if (TAG)
+            for (int t = 0; t < __popc(k0); ++t)
+              if (idx + t < cap) tags[idx + t] = d0;
           idx += __popc(k0);
         }
         if (k1) {
@@ -1322,6 +1330,9 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
           for (int e = 0; e < 8; ++e) q0[kRow + e] = s1[e];
           write_triangles<LOGB>(L.bricks, r0 + 32 * kRow, q0 + kRow, iso, sh.packed[c1], k1, idx, cap, tris,
                                 mc.edge_a, mc.edge_b);
+          if (TAG)
+            for (int t = 0; t < __popc(k1); ++t)
+              if (idx + t < cap) tags[idx + t] = d1;
         }
         __syncwarp();
       }
@@ -1736,11 +1747,19 @@ cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, const i
 
 cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, float iso, float* tris,
                       long long cap, unsigned long long* counter, unsigned char* cases,
-                      unsigned char* ntri, const McConst& mc, int grid, cudaStream_t st) {
+                      unsigned char* ntri, const McConst& mc, int grid, cudaStream_t st, long long* tags) {
   if (nd <= 0) return cudaSuccess;
   if (cases || ntri) {
     AMR_DISPATCH(logb, (k_mc<LB, false, true><<<grid, 256, 0, st>>>(loc, duals, nd, iso, tris, cap, counter,
-                                                                     cases, ntri, mc)));
+                                                                     cases, ntri, nullptr, mc)));
+  } else if (tags) {
+    AMR_DISPATCH(logb, ({
+      const cudaError_t e = cudaFuncSetAttribute(k_mc<LB, true, false, false, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMcSmemBytes);
+      if (e != cudaSuccess) return e;
+      k_mc<LB, true, false, false, true><<<grid, 256, kMcSmemBytes, st>>>(loc, duals, nd, iso, tris, cap, counter,
+                                                                         nullptr, nullptr, tags, mc);
+    }));
   } else {
     // dynamic shared memory above the 48 KB default (an attribute of the
     // current device's context, so set on every launch)
@@ -1749,7 +1768,7 @@ cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, f
           cudaFuncSetAttribute(k_mc<LB, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMcSmemBytes);
       if (e != cudaSuccess) return e;
       k_mc<LB, true, false><<<grid, 256, kMcSmemBytes, st>>>(loc, duals, nd, iso, tris, cap, counter, cases, ntri,
-                                                             mc);
+                                                             nullptr, mc);
     }));
   }
   return cudaGetLastError();
@@ -1764,7 +1783,7 @@ cudaError_t launch_mc_keys(int logb, Locator loc, const uint4* duals, long long 
         cudaFuncSetAttribute(k_mc<LB, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMcSmemBytes);
     if (e != cudaSuccess) return e;
     k_mc<LB, true, false, true><<<grid, 256, kMcSmemBytes, st>>>(loc, duals, nd, iso, reinterpret_cast<float*>(tkeys),
-                                                                  cap, counter, nullptr, nullptr, mc);
+                                                                  cap, counter, nullptr, nullptr, nullptr, mc);
   }));
   return cudaGetLastError();
 }

@@ -114,10 +114,11 @@ cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, const i
                                   uint4* duals, long long cap, Scratch* sc, float iso, float* tris,
                                   long long tri_cap, const McConst& mc, cudaStream_t st);
 
+// tags (may be NULL): per written triangle the index of its dual in `duals`.
 cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, float iso,
                       float* tris, long long cap, unsigned long long* counter,
                       unsigned char* cases, unsigned char* ntri, const McConst& mc, int grid,
-                      cudaStream_t st);
+                      cudaStream_t st, long long* tags = nullptr);
 
 // Indexed face set (three passes): the kept triangles' edge keys (u64 slot
 // pairs, smaller first) into tkeys[cap][3] through `counter`; the keys into

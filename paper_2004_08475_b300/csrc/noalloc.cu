@@ -76,20 +76,25 @@ int scratch_for_current_device(unsigned char** out) {
   return AMR_OK;
 }
 
-McConst table_const() {
-  McTable t;
-  make_mc_table(&t);
-  McConst m;
-  for (int c = 0; c < 256; ++c) {
-    m.packed[c] = t.packed[c];
-    m.count[c] = t.count[c];
-  }
-  m.edge_a = m.edge_b = 0;
-  for (int k = 0; k < 12; ++k) {
-    m.edge_a |= (unsigned long long)t.edge_a[k] << (4 * k);
-    m.edge_b |= (unsigned long long)t.edge_b[k] << (4 * k);
-  }
-  return m;
+// The Marching Cubes table in kernel form, generated once per process (a
+// function-local static: initialised on first use, thread-safe).
+const McConst& table_const() {
+  static const McConst table = [] {
+    McTable t;
+    make_mc_table(&t);
+    McConst m;
+    for (int c = 0; c < 256; ++c) {
+      m.packed[c] = t.packed[c];
+      m.count[c] = t.count[c];
+    }
+    m.edge_a = m.edge_b = 0;
+    for (int k = 0; k < 12; ++k) {
+      m.edge_a |= (unsigned long long)t.edge_a[k] << (4 * k);
+      m.edge_b |= (unsigned long long)t.edge_b[k] << (4 * k);
+    }
+    return m;
+  }();
+  return table;
 }
 
 int rc_of(cudaError_t e) {
@@ -191,7 +196,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
   }
   long long nt = 0;
   if (nd > 0) {
-    const McConst mc = table_const();
+    const McConst& mc = table_const();
     const int grid_d = (int)std::max(1ll, std::min((nd + 255) / 256, (long long)sms * 8));
     NA_TRY(rc_of(launch_mc(kLogB, L, duals, nd, iso, tris, cap, &sc->n_tri[0], nullptr, nullptr, mc, grid_d,
                            st)));

@@ -269,7 +269,8 @@ class Server:
         padded = isos + [float("inf")] * (bucket - k)   # +inf: no corner is above it, no triangles
         h_isos[:bucket] = torch.tensor(padded, dtype=torch.float32)
         d_isos[:bucket].copy_(h_isos[:bucket], non_blocking=True)
-        key = (w, bucket, out.data_ptr())
+        # the graph bakes in the buffer's address and capacity: both are in the key
+        key = (w, bucket, out.data_ptr(), int(out.shape[0]))
         g = res.graphs.get(key) if self.use_graphs else None
         if g is not None:
             g.replay()
@@ -285,7 +286,10 @@ class Server:
             with self.cuda_lock:
                 out = torch.empty((int(offs[bucket] * 1.25) + 1, 3, 3), dtype=torch.float32,
                                   device=self.device)
-            res.graphs.clear()
+            with self.cv:   # this worker's graphs on every resident data set point at the old buffer
+                for other in self.resident.values():
+                    for gk in [gk for gk in other.graphs if gk[0] == w]:
+                        del other.graphs[gk]
             ctx.iso_batch_async(d_isos[:bucket], out, d_offs[:bucket + 1])
             h_offs[:bucket + 1].copy_(d_offs[:bucket + 1], non_blocking=True)
             stream.synchronize()

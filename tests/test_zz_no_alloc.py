@@ -5,9 +5,9 @@ managed by someone else, or latency-critical code that may not allocate).
 The entry point takes every intermediate buffer from a fixed array the
 library reserves per GPU. These tests call it through the C ABI, twice in a
 row on different data sets (so left-over contents of the shared array would
-show), and compare with the regular context entry points: equal triangle
-counts, and triangles equal within 1e-5 of the extent after canonical
-ordering. Kept in a file of its own, collected last."""
+show), and compare with the regular context entry points and with the
+oracle: equal triangle counts, and triangles equal within 1e-5 of the extent
+after canonical ordering. Kept in a file of its own, collected last."""
 import ctypes
 
 import numpy as np
@@ -15,7 +15,7 @@ import pytest
 import torch
 
 from paper_2004_08475_b300 import synth
-from tests.parity import canonical
+from tests.parity import canonical, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +54,10 @@ def test_noalloc_matches_context_two_calls():
         got = out[:n].cpu().numpy()
         extent = float(max(info["domain"]))
         diff = np.abs(canonical(got).astype(np.float64) - canonical(want).astype(np.float64)).max()
+        assert diff <= 1e-5 * extent
+        ref = run_oracle(xyz, lv, s, iso)["tris"]
+        assert ref.shape[0] == n
+        diff = np.abs(canonical(got).astype(np.float64) - canonical(ref).astype(np.float64)).max()
         assert diff <= 1e-5 * extent
 
 
