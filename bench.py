@@ -69,8 +69,9 @@ def algorithmic_bytes(kernel: str, n: int, n_slots: int, nd: int, nt: int, place
         "k_scatter_cells": 17.0 * n + 8.0 * n,       # read the cell, write id + scalar
         "k_bin_coarse": 8.0 * n + 12.0 * n,          # read code + scalar, write a 12-byte entry
         "k_bin_fine": 12.0 * n + 12.0 * n,           # re-split the entries by window
-        "k_place_windows": 12.0 * n + 8.0 * n_slots, # read the entries, write every slot's record
+        "k_place_windows": 12.0 * n + 16.0 * n_slots,  # read the entries, write record + view + scalar per slot
         "k_resolve_views": 16.0 * n_slots,           # read the record, write view + scalar
+        "k_resolve_empty": 4.0 * (n_slots - n),      # the empty slots' views (at least)
         "k_order_count": 16.0 * n_slots / b3,        # read each brick's record
         "k_order_scan": 8.0 * 32768,                 # read and write the bucket counters
         "k_order_scatter": 20.0 * n_slots / b3,      # read each brick's record, write its position
@@ -98,9 +99,9 @@ def paper_bytes(stage: str, n: int, nd: int, nt: int) -> float:
 
 # kernels whose work is exactly one stage of the method
 PAPER_STAGE = {"k_mc": "mc", "k_dual_cells": "dual"}
-LOCATOR_KERNELS = ("k_insert_bricks", "k_insert_bin", "k_scatter_cells", "k_bin_coarse", "k_bin_fine",
-                   "k_place_windows", "k_resolve_views", "k_resolve_empty", "k_brick_neighbors",
-                   "k_order_count", "k_order_scan", "k_order_scatter")
+LOCATOR_KERNELS = ("k_insert_bricks", "k_scatter_cells", "k_bin_coarse", "k_bin_fine", "k_place_windows",
+                   "k_resolve_views", "k_resolve_empty", "k_brick_neighbors", "k_order_count", "k_order_scan",
+                   "k_order_scatter")
 
 
 def load_peaks():
@@ -395,47 +396,57 @@ def run_reference(args, workload_desc, gen):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    """Serving workload: 24 data sets of 50k..50M cells, Zipf(1) popularity,
-    Poisson arrivals of requests with 1-16 iso-values; the continuous-batching
-    server against per-request plain extraction (FIFO), at 0.5/0.8/0.95 of the
-    plain path's measured capacity, plus one run under an 8 GB budget."""
-    from paper_2004_08475_b300 import serve
-    torch.cuda.set_device(0)
-    sets = synth.serving_set(device="cuda")
-    host = {name: (x.cpu().pin_memory(), l.cpu().pin_memory(), v.cpu().pin_memory())
-            for name, x, l, v, _ in sets}
-    iso_rng = {name: r for name, _, _, _, r in sets}
-    names = [t[0] for t in sets]
-    del sets
-    torch.cuda.empty_cache()
-    rng = np.random.default_rng(5)
-    pop = 1.0 / np.arange(1, len(names) + 1)
-    perm = rng.permutation(len(names))                       # popularity unrelated to size
-    prob = np.empty(len(names))
-    prob[perm] = pop / pop.sum()
+class ServeBench:
+    """The serving workload: 24 data sets of 50k..50M cells cut from the
+    octree and block generators, Zipf(1) popularity (unrelated to size),
+    requests of 1-16 iso-values (40th-95th percentile of the data set's
+    scalar) arriving as a Poisson stream; the continuous-batching server
+    against per-request plain extraction (FIFO). The plain path's capacity
+    (requests/s, back to back) sets the arrival rates."""
 
-    def make(nreq, arrivals):
+    def __init__(self, slots: int, sample: int, seed: int = 5):
+        from paper_2004_08475_b300 import serve
+        self.serve = serve
+        self.slots = slots
+        sets = synth.serving_set(device="cuda")
+        self.host = {name: (x.cpu().pin_memory(), l.cpu().pin_memory(), v.cpu().pin_memory())
+                     for name, x, l, v, _ in sets}
+        self.iso_rng = {name: r for name, _, _, _, r in sets}
+        self.names = [t[0] for t in sets]
+        self.cells = sum(int(v[0].shape[0]) for v in self.host.values())
+        del sets
+        torch.cuda.empty_cache()
+        self.rng = np.random.default_rng(seed)
+        pop = 1.0 / np.arange(1, len(self.names) + 1)
+        perm = self.rng.permutation(len(self.names))
+        self.prob = np.empty(len(self.names))
+        self.prob[perm] = pop / pop.sum()
+        reqs = self.make(sample, np.zeros(sample))   # plain capacity: back-to-back service of a sample
+        t0 = time.perf_counter()
+        for r in reqs:
+            r.t_arrival = t0
+        serve.serve_plain(self.host, reqs)
+        self.cap_plain = len(reqs) / (max(r.t_done for r in reqs) - t0)
+
+    def make(self, nreq, arrivals):
         reqs = []
         for i in range(nreq):
-            name = names[rng.choice(len(names), p=prob)]
-            a, b = iso_rng[name]
-            isos = list(rng.uniform(a, b, size=int(rng.integers(1, 17))))
-            reqs.append(serve.Request(i, name, [float(v) for v in isos], float(arrivals[i])))
+            name = self.names[self.rng.choice(len(self.names), p=self.prob)]
+            a, b = self.iso_rng[name]
+            isos = list(self.rng.uniform(a, b, size=int(self.rng.integers(1, 17))))
+            reqs.append(self.serve.Request(i, name, [float(v) for v in isos], float(arrivals[i])))
         return reqs
 
-    # plain capacity: back-to-back service of a sample
-    sample = make(args.serve_sample, np.zeros(args.serve_sample))
-    t0 = time.perf_counter()
-    for r in sample:
-        r.t_arrival = t0
-    serve.serve_plain(host, sample)
-    cap_plain = len(sample) / (max(r.t_done for r in sample) - t0)
+    def poisson(self, nreq, load):
+        return self.make(nreq, np.cumsum(self.rng.exponential(1.0 / (load * self.cap_plain), size=nreq)))
 
-    def run_server(reqs, budget):
-        srv = serve.Server(budget_bytes=budget, slots=args.serve_slots)
-        for name, (x, l, v) in host.items():
-            srv.datasets[name] = serve._Dataset(name, x, l, v, {})
+    def clone(self, reqs):
+        return [self.serve.Request(r.rid, r.dataset, list(r.isos), r.t_arrival) for r in reqs]
+
+    def run_server(self, reqs, budget):
+        srv = self.serve.Server(budget_bytes=budget, slots=self.slots)
+        for name, (x, l, v) in self.host.items():
+            srv.datasets[name] = self.serve._Dataset(name, x, l, v, {})
         srv.start()
         t_base = time.perf_counter() + 0.05
         for r in reqs:
@@ -451,36 +462,54 @@ def run_serve(args):
             r.done.wait()
         stats = dict(srv.stats)
         srv.stop()
-        return {**serve.latency_summary(reqs), "stats": stats}
+        return {**self.serve.latency_summary(reqs), "stats": stats}
 
-    def run_plain(reqs):
+    def run_plain(self, reqs):
         t_base = time.perf_counter() + 0.05
         for r in reqs:
             r.t_arrival += t_base
-        serve.serve_plain(host, reqs)
-        return serve.latency_summary(reqs)
+        self.serve.serve_plain(self.host, reqs)
+        return self.serve.latency_summary(reqs)
 
+    def config(self):
+        return {"workload": "serving: 24 data sets 50k-50M cells (octree / block crops), Zipf(1), Poisson "
+                            "arrivals, 1-16 iso-values per request",
+                "cells": self.cells, "slots": self.slots, "budget_gb": 120}
+
+
+def serve_leg(args, gpu_index):
+    """The serving measurement carried by the default line: server and plain
+    p50/p99 latency and triangles/s at 0.8 of the plain path's capacity, and
+    both at saturation (every request waiting at t = 0; throughput =
+    triangles / makespan), with the SM clocks sampled meanwhile."""
+    sb = ServeBench(args.serve_slots, args.serve_sample)
+    with ClockSampler(gpu_index) as clk:
+        reqs = sb.poisson(args.serve_line_requests, 0.8)
+        at08 = {"requests": len(reqs), "rate_per_s": 0.8 * sb.cap_plain,
+                "server": sb.run_server(sb.clone(reqs), 120 << 30), "plain": sb.run_plain(reqs)}
+        sat = sb.make(args.serve_saturation_requests, np.zeros(args.serve_saturation_requests))
+        satr = {"requests": len(sat), "server": sb.run_server(sb.clone(sat), 120 << 30), "plain": sb.run_plain(sat)}
+    return {"config": sb.config(), "plain_capacity_req_per_s": sb.cap_plain, "load_0.8": at08, "saturation": satr,
+            "clocks": clk.summary()}
+
+
+def run_serve(args):
+    """--mode serve: the serving workload at 0.5/0.8/0.95 of the plain path's
+    capacity, one run under an 8 GB budget (LRU evictions), and saturation."""
+    torch.cuda.set_device(0)
+    sb = ServeBench(args.serve_slots, args.serve_sample)
     results = {}
-    for load in (0.5, 0.8, 0.95):
-        rate = load * cap_plain
-        arr = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_requests))
-        reqs = make(args.serve_requests, arr)
-        clone = [serve.Request(r.rid, r.dataset, list(r.isos), r.t_arrival) for r in reqs]
-        results[str(load)] = {"rate_per_s": rate, "server": run_server(reqs, 120 << 30),
-                              "plain": run_plain(clone)}
-    arr = np.cumsum(rng.exponential(1.0 / (0.8 * cap_plain), size=args.serve_requests))
-    results["0.8_budget_8GB"] = {"server": run_server(make(args.serve_requests, arr), 8 << 30)}
-    # saturation: every request waiting at t = 0; throughput = triangles / makespan
-    reqs = make(args.serve_requests, np.zeros(args.serve_requests))
-    clone = [serve.Request(r.rid, r.dataset, list(r.isos), r.t_arrival) for r in reqs]
-    results["saturation"] = {"server": run_server(reqs, 120 << 30), "plain": run_plain(clone)}
+    with ClockSampler(0) as clk:
+        for load in (0.5, 0.8, 0.95):
+            reqs = sb.poisson(args.serve_requests, load)
+            results[str(load)] = {"rate_per_s": load * sb.cap_plain,
+                                  "server": sb.run_server(sb.clone(reqs), 120 << 30), "plain": sb.run_plain(reqs)}
+        results["0.8_budget_8GB"] = {"server": sb.run_server(sb.poisson(args.serve_requests, 0.8), 8 << 30)}
+        reqs = sb.make(args.serve_requests, np.zeros(args.serve_requests))
+        results["saturation"] = {"server": sb.run_server(sb.clone(reqs), 120 << 30), "plain": sb.run_plain(reqs)}
     line = {"mode": "serve", "metric": METRIC, "unit": "ms (p50/p99 latency), triangles/s",
-            "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "serving: 24 data sets 50k-50M cells (octree / block crops), Zipf(1), "
-                                   "Poisson arrivals, 1-16 iso-values per request",
-                       "requests_per_load": args.serve_requests, "slots": args.serve_slots,
-                       "budget_gb": 120},
-            "plain_capacity_req_per_s": cap_plain, "loads": results,
+            "n_gpus": 1, "data": "synthetic", "config": {**sb.config(), "requests_per_load": args.serve_requests},
+            "plain_capacity_req_per_s": sb.cap_plain, "loads": results, "clocks": clk.summary(),
             "gpu": torch.cuda.get_device_name(0)}
     print(json.dumps(line), flush=True)
 
@@ -507,6 +536,10 @@ def main():
     ap.add_argument("--batch-isos", type=int, default=16)
     ap.add_argument("--mode", default="step", choices=["step", "serve"])
     ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-line-requests", type=int, default=2000,
+                    help="requests at 0.8 load in the serving object of the default line")
+    ap.add_argument("--serve-saturation-requests", type=int, default=1000)
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving object out of the default line")
     ap.add_argument("--serve-sample", type=int, default=80)
     ap.add_argument("--serve-slots", type=int, default=3)
     args = ap.parse_args()
@@ -605,7 +638,7 @@ def main():
     staged = [k for k in kernels if k in PAPER_STAGE] or list(kernels)
     dom = max(staged, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
     dk = kernels[dom]
-    units = {"k_insert_bricks": n, "k_insert_bin": n, "k_scatter_cells": n, "k_bin_coarse": n, "k_bin_fine": n,
+    units = {"k_insert_bricks": n, "k_scatter_cells": n, "k_bin_coarse": n, "k_bin_fine": n,
              "k_place_windows": inf.n_slots, "k_resolve_views": inf.n_slots,
              "k_dual_cells": inf.n_slots, "k_dual_cells_iso": inf.n_slots, "k_mc": nd}.get(dom, n)
     ach = dk.get("paper_gbs", dk["gbs"])
@@ -739,6 +772,12 @@ def main():
         ectx.close()
         del hx, hl, hs, hout
 
+    serve_obj = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        ctx.trim()
+        torch.cuda.empty_cache()
+        serve_obj = serve_leg(args, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x, l, v = xyz.cpu().numpy(), lv.cpu().numpy(), s.cpu().numpy()
@@ -780,6 +819,7 @@ def main():
             "kernels": kernels,
             "batched_iso": batch,
             "indexed_face_set": indexed,
+            "serve": serve_obj,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),

@@ -43,7 +43,10 @@ extern "C" {
 #define AMR_ERR_OOM          (-8)  /* device allocation failed */
 #define AMR_ERR_CAPACITY     (-9)  /* output buffer too small; the exact
                                       required count is still reported */
-#define AMR_ERR_TIMEOUT      (-10) /* a bounded device wait ran out */
+#define AMR_ERR_TIMEOUT      (-10) /* reserved for a bounded device wait that
+                                      runs out; no kernel of this version
+                                      waits on another thread, so no entry
+                                      point returns it */
 #define AMR_ERR_CUDA         (-11) /* any other CUDA runtime error */
 
 /* ---- flags --------------------------------------------------------------- */
@@ -66,7 +69,7 @@ typedef struct amr_locator_opts {
                            shared memory and written whole), < 0 always a
                            direct scatter, 0 binned from 2^20 cells on; the
                            binned form needs a brick table of at most
-                           2^(32 - 3 log2_brick) entries and otherwise falls
+                           2^(31 - 3 log2_brick) entries and otherwise falls
                            back to the direct scatter                   [0] */
 } amr_locator_opts;
 
@@ -113,6 +116,20 @@ int amr_build_locator(amr_ctx* ctx, const amr_locator_opts* opts);
  * dual list stays resident in the context for later amr_iso calls.
  * *n_dual receives the number of dual cells. Synchronises the stream. */
 int amr_dual_cells(amr_ctx* ctx, int64_t* n_dual);
+
+/* amr_dual_cells restricted to one owner slab, for a data set sharded into
+ * x slabs (one GPU per slab, or one after another): only the cells whose
+ * lower corner's x lies in [x_begin, x_end) emit their dual cells (the
+ * emitting cell of a dual is its owner, Sec. 4.4: the unique cell that rule
+ * 3 lets emit it); every uploaded cell still takes part in the rules. A
+ * shard that holds every cell overlapping [x_begin - w_max, x_end + w_max),
+ * w_max the widest cell of the whole data set, emits exactly the whole data
+ * set's dual cells owned in its slab (every vertex of such a dual contains a
+ * point within one owner width of the owner, Sec. 4.2-4.4), so the slabs'
+ * lists together are the whole list, each dual once. Outputs and resident
+ * state as amr_dual_cells. No counterpart in the paper's GPU code (it runs
+ * one GPU). */
+int amr_dual_cells_owned(amr_ctx* ctx, int32_t x_begin, int32_t x_end, int64_t* n_dual);
 
 /* amr_dual_cells and amr_iso(iso) in one pass over the locator: every dual
  * cell is emitted into the resident list (exactly as amr_dual_cells) and
@@ -225,7 +242,9 @@ int amr_iso_batch(amr_ctx* ctx, const float* isos, int n_iso, float* tris,
 
 /* amr_iso_batch without any host synchronisation or allocation, for use
  * inside a captured CUDA graph: the iso-values are read from device memory
- * when the work runs, and the segment offsets are computed on the device.
+ * when the work runs, and the segment offsets are computed on the device
+ * (three kernels: per-tile counts, their prefix sums, emission; the
+ * workspace was sized by amr_dual_cells).
  *   d_isos    [n_iso] device array, 1 <= n_iso <= 64
  *   tris      [cap][3][3] device output; iso k's triangles are rows
  *             d_offsets[k] .. d_offsets[k+1]-1 (rows past cap are dropped)
@@ -236,6 +255,32 @@ int amr_iso_batch(amr_ctx* ctx, const float* isos, int n_iso, float* tris,
  * enqueuing. */
 int amr_iso_batch_async(amr_ctx* ctx, const float* d_isos, int n_iso,
                         float* tris, int64_t cap, int64_t* d_offsets);
+
+/* Several data sets' batches in one launch per pass (no counterpart in the
+ * paper; the batching of many small data sets that serving needs): job j
+ * runs Marching Cubes at n_iso iso-values over the resident dual cells of
+ * jobs[j].ctx; all jobs' duals are cut into tiles that one grid shares, so
+ * small data sets fill the GPU together.
+ *   jobs      [n_jobs] host array, 1 <= n_jobs <= 32; every ctx after
+ *             amr_dual_cells, all on one device; sum of n_iso <= 64
+ *   d_isos    device array of the batch's iso-values: job 0's n_iso values,
+ *             then job 1's, ...; value q of the batch is segment q
+ *   tris      [cap][3][3] device output; segment q is rows d_offsets[q] ..
+ *             d_offsets[q+1]-1 (rows past cap are dropped)
+ *   d_offsets [segments + 1] device int64, written by the device
+ *   workspace device memory of at least amr_iso_multi_workspace(jobs,
+ *             n_jobs) bytes, owned by the caller (the call allocates nothing)
+ *   cuda_stream the stream all work is enqueued on (NULL = legacy stream)
+ * Neither synchronises nor allocates; returns after enqueuing. The result is
+ * the same, segment by segment, as amr_iso_batch on each context alone. */
+typedef struct amr_iso_job {
+  amr_ctx* ctx;
+  int n_iso;
+} amr_iso_job;
+int64_t amr_iso_multi_workspace(const amr_iso_job* jobs, int n_jobs);
+int amr_iso_multi_async(const amr_iso_job* jobs, int n_jobs, const float* d_isos, float* tris,
+                        int64_t cap, int64_t* d_offsets, void* workspace,
+                        int64_t workspace_bytes, void* cuda_stream);
 
 /* Waits for all work queued on the context's stream. */
 int amr_sync(amr_ctx* ctx);
@@ -254,7 +299,7 @@ const char* amr_strerror(int code);
  * of the build); a binding compares it with the header it was written for
  * and refuses a library built from other sources. No counterpart in the
  * paper. */
-#define AMR_ABI_VERSION 9
+#define AMR_ABI_VERSION 11
 int amr_abi_version(void);
 
 /* ---- introspection (host only, no device needed) ------------------------ */

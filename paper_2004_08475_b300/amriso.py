@@ -43,6 +43,10 @@ HOST_PTRS = 1
 COPY = 2
 
 
+class _IsoJob(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("n_iso", ctypes.c_int)]
+
+
 class AmrError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {strerror(code)} ({code})")
@@ -62,7 +66,7 @@ class _Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("placement", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-ABI_VERSION = 9   # AMR_ABI_VERSION of include/amriso.h
+ABI_VERSION = 11   # AMR_ABI_VERSION of include/amriso.h
 
 
 def _load() -> ctypes.CDLL:
@@ -78,6 +82,7 @@ def _load() -> ctypes.CDLL:
         "amr_upload": (I, [P, P, P, P, I64, I]),
         "amr_build_locator": (I, [P, ctypes.POINTER(_LocatorOpts)]),
         "amr_dual_cells": (I, [P, ctypes.POINTER(I64)]),
+        "amr_dual_cells_owned": (I, [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(I64)]),
         "amr_get_duals": (I, [P, P, I64, I]),
         "amr_dual_cells_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), I]),
         "amr_iso": (I, [P, F, P, I64, ctypes.POINTER(I64), I]),
@@ -88,6 +93,8 @@ def _load() -> ctypes.CDLL:
         "amr_iso_cases": (I, [P, F, P, P, I]),
         "amr_iso_batch": (I, [P, P, I, P, I64, P, I]),
         "amr_iso_batch_async": (I, [P, P, I, P, I64, P]),
+        "amr_iso_multi_workspace": (I64, [P, I]),
+        "amr_iso_multi_async": (I, [P, I, P, P, I64, P, P, I64, P]),
         "amr_sync": (I, [P]),
         "amr_trim": (I, [P]),
         "amr_strerror": (ctypes.c_char_p, [I]),
@@ -117,7 +124,8 @@ EXPORTS = ("amr_create", "amr_destroy", "amr_set_stream", "amr_upload", "amr_bui
            "amr_sync", "amr_strerror", "amr_mc_table", "amr_get_info", "amr_enable_timing",
            "amr_kernel_times", "amr_kernel_name", "amr_extract_noalloc", "amr_iso_batch_async",
            "amr_dual_cells_iso", "amr_trim", "amr_abi_version", "amr_iso_indexed",
-           "amr_interpolate", "amr_dual_shapes", "amr_iso_tagged")
+           "amr_interpolate", "amr_dual_shapes", "amr_iso_tagged", "amr_iso_multi_workspace",
+           "amr_iso_multi_async", "amr_dual_cells_owned")
 
 
 def lib() -> ctypes.CDLL:
@@ -147,6 +155,37 @@ def _ptr(t) -> int:
     if isinstance(t, np.ndarray):
         return t.ctypes.data
     return t.data_ptr()
+
+
+def _jobs(contexts, n_isos):
+    arr = (_IsoJob * len(contexts))()
+    for j, (c, k) in enumerate(zip(contexts, n_isos)):
+        arr[j].ctx = c._h
+        arr[j].n_iso = int(k)
+    return arr
+
+
+def iso_multi_workspace(contexts, n_isos) -> int:
+    """Device bytes amr_iso_multi_async needs for these (context, iso count)
+    jobs."""
+    r = _lib.amr_iso_multi_workspace(_jobs(contexts, n_isos), len(contexts))
+    if r < 0:
+        _check(int(r), "amr_iso_multi_workspace")
+    return int(r)
+
+
+def iso_multi_async(contexts, n_isos, d_isos: torch.Tensor, out: torch.Tensor, d_offsets: torch.Tensor,
+                    workspace: torch.Tensor, stream: torch.cuda.Stream | None = None):
+    """Enqueue one batch over several data sets: job j = contexts[j] at its
+    n_isos[j] iso-values (consecutive in d_isos); segment q of the batch is
+    out[d_offsets[q]:d_offsets[q+1]]. Neither synchronises nor allocates."""
+    assert d_isos.is_cuda and d_isos.dtype == torch.float32 and d_offsets.dtype == torch.int64
+    assert d_offsets.numel() >= sum(n_isos) + 1 and out.is_cuda and workspace.is_cuda
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.amr_iso_multi_async(_jobs(contexts, n_isos), len(contexts), _ptr(d_isos), _ptr(out),
+                                    int(out.shape[0]), _ptr(d_offsets), _ptr(workspace),
+                                    int(workspace.numel() * workspace.element_size()),
+                                    ctypes.c_void_p(st.cuda_stream)), "amr_iso_multi_async")
 
 
 @dataclass
@@ -223,9 +262,15 @@ class AmrContext:
         rc = _lib.amr_build_locator(self._h, ctypes.byref(o))
         _check(rc, "amr_build_locator")
 
-    def dual_cells(self) -> int:
+    def dual_cells(self, owned_x: tuple | None = None) -> int:
+        """Dual cells (kept resident); owned_x = (x_begin, x_end) keeps only
+        those whose owning cell's lower corner x lies in [x_begin, x_end)."""
         n = ctypes.c_int64(0)
-        _check(_lib.amr_dual_cells(self._h, ctypes.byref(n)), "amr_dual_cells")
+        if owned_x is None:
+            _check(_lib.amr_dual_cells(self._h, ctypes.byref(n)), "amr_dual_cells")
+        else:
+            _check(_lib.amr_dual_cells_owned(self._h, int(owned_x[0]), int(owned_x[1]), ctypes.byref(n)),
+                   "amr_dual_cells_owned")
         self.n_dual = n.value
         return n.value
 

@@ -32,14 +32,14 @@ enum KernelId {
   KT_INSERT = 0, KT_SCATTER, KT_RESOLVE, KT_DUAL, KT_MC, KT_MC_CASES, KT_BATCH_COUNT, KT_BATCH_EMIT,
   KT_GET_DUALS, KT_NEIGHBORS, KT_BIN, KT_PLACE, KT_DUAL_ISO, KT_BIN_FINE, KT_MC_KEYS, KT_WELD_INSERT,
   KT_WELD_INDEX, KT_INTERPOLATE, KT_SHAPES, KT_ORDER_COUNT, KT_ORDER_SCAN, KT_ORDER_SCATTER, KT_MC_TAGGED,
-  KT_COUNT
+  KT_RESOLVE_EMPTY, KT_BATCH_SCAN, KT_COUNT
 };
 const char* const kKernelNames[KT_COUNT] = {
     "k_insert_bricks", "k_scatter_cells", "k_resolve_views", "k_dual_cells", "k_mc",
-    "k_mc_cases",      "k_mc_batch_count", "k_mc_batch_emit", "k_get_duals", "k_brick_neighbors",
+    "k_mc_cases",      "k_batch_count", "k_batch_emit", "k_get_duals", "k_brick_neighbors",
     "k_bin_coarse", "k_place_windows", "k_dual_cells_iso", "k_bin_fine", "k_mc_keys", "k_weld_insert",
     "k_weld_index", "k_interpolate", "k_dual_shapes", "k_order_count", "k_order_scan", "k_order_scatter",
-    "k_mc_tagged"};
+    "k_mc_tagged", "k_resolve_empty", "k_batch_scan"};
 
 const McTable& host_table() {
   static McTable t = [] {
@@ -84,7 +84,8 @@ struct amr_ctx {
   float alpha = 0.5f;
   int block = 256;
   int check_overlap = 0;
-  DevBuf htab, bricks, rec, scal, view, nbr, staging, codes;
+  DevBuf htab, bricks, rec, scal, view, nbr;
+  DevBuf staging, codes, elist;   // binned placement workspace
   DevBuf border, bcount;   // bricks in spatial order (the dual pass's visiting order), bucket counters
   int placement = 0;   // 0 direct scatter, 1 binned
   unsigned long long hcap = 0;
@@ -97,6 +98,7 @@ struct amr_ctx {
   DevBuf scratch;
   Scratch* host_sc = nullptr;  // pinned mirror
   DevBuf stage_buf, iso_buf, seg_buf;
+  DevBuf bwork;   // batched iso-values: per-tile counters and row offsets for up to kMaxIso values
   DevBuf tkeys, wtab, ostage;   // indexed face set: triangle edge keys, weld table, host-delivery staging
   long long tkeys_cap = 0;
   McConst mc;
@@ -203,7 +205,6 @@ int err_code(unsigned e) {
   if (e & ERR_UNALIGNED) return AMR_ERR_UNALIGNED;
   if (e & ERR_DUPLICATE) return AMR_ERR_DUPLICATE;
   if (e & ERR_OVERLAP) return AMR_ERR_OVERLAP;
-  if (e & ERR_TIMEOUT) return AMR_ERR_TIMEOUT;
   if (e & ERR_HASH_FULL) return AMR_ERR_CAPACITY;
   return AMR_OK;
 }
@@ -232,6 +233,15 @@ unsigned long long pow2_at_least(unsigned long long v) {
   return p;
 }
 
+// Copies a Marching Cubes launch's triangle counter back and waits.
+int mc_result(amr_ctx* c, const unsigned long long* counter, long long* nt) {
+  AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           c->stream));
+  AMR_CUDA(cudaStreamSynchronize(c->stream));
+  *nt = (long long)c->host_sc->n_tri[0];
+  return AMR_OK;
+}
+
 // Copies `bytes` from device `src` to `dst` (device or host per flags).
 int deliver(amr_ctx* c, void* dst, const void* src, size_t bytes, int flags) {
   if (bytes == 0 || dst == src) return AMR_OK;
@@ -258,7 +268,7 @@ const char* amr_strerror(int code) {
     case AMR_ERR_STATE: return "call out of order";
     case AMR_ERR_OOM: return "device out of memory";
     case AMR_ERR_CAPACITY: return "output capacity exceeded";
-    case AMR_ERR_TIMEOUT: return "bounded device wait timed out";
+    case AMR_ERR_TIMEOUT: return "bounded device wait timed out (reserved)";
     case AMR_ERR_CUDA: return "CUDA runtime error";
     default: return "unknown error";
   }
@@ -303,8 +313,9 @@ void amr_destroy(amr_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
-                    &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals, &c->scratch,
-                    &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->tkeys, &c->wtab,
+                    &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes,
+                    &c->elist, &c->duals, &c->scratch,
+                    &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->bwork, &c->tkeys, &c->wtab,
                     &c->ostage, &c->border, &c->bcount};
   for (DevBuf* b : bufs) release(*b);
   if (c->host_sc) cudaFreeHost(c->host_sc);
@@ -335,6 +346,7 @@ int amr_trim(amr_ctx* c) {
   AMR_CUDA(cudaStreamSynchronize(c->stream));
   release(c->staging);
   release(c->codes);
+  release(c->elist);
   release(c->stage_buf);
   release(c->tkeys);
   release(c->wtab);
@@ -409,7 +421,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   for (int attempt = 0;; ++attempt) {
     c->hcap = pow2_at_least(want);
     codes = nullptr;
-    if (binned && n > 0 && c->hcap <= (1ull << (32 - 3 * logb))) {
+    if (binned && n > 0 && c->hcap <= (1ull << (31 - 3 * logb))) {   // codes: slot or table entry below 2^31
       AMR_TRY(ensure(c->codes, (size_t)n * 4));
       codes = static_cast<unsigned*>(c->codes.p);
     }
@@ -450,17 +462,19 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   AMR_TRY(ensure(c->rec, (size_t)c->n_slots * 8));
   AMR_TRY(ensure(c->scal, (size_t)c->n_slots * 4));
   AMR_TRY(ensure(c->view, (size_t)c->n_slots * 4));
+  const bool binned_ok = binned && codes != nullptr;
   if (c->n_slots) {
-    const Locator L = make_locator(c);
-    // binned placement unless asked otherwise or the input is small
-    // binned placement needs the insert pass's cell codes; a table too large
-    // for them (after rebuilds) falls back to the direct scatter
-    c->placement = binned && codes ? 1 : 0;
-    if (binned && codes) {
+    // binned placement unless asked otherwise or the input is small; it
+    // needs the insert pass's cell codes, so a table too large for them
+    // (after rebuilds) falls back to the direct scatter
+    c->placement = binned_ok ? 1 : 0;
+    if (binned_ok) {
       AMR_TRY(ensure(c->staging, bin_layout(c->n_slots).bytes));
+      AMR_TRY(ensure(c->elist, (size_t)c->n_bricks * 4));
+      const Locator L0 = make_locator(c);
       {
         KernelTimer kt(c, KT_BIN);
-        AMR_CUDA(launch_bin_coarse(logb, c->s, n, L, c->n_slots, c->staging.p, dev_sc(c), c->sm_count, codes,
+        AMR_CUDA(launch_bin_coarse(logb, c->s, n, L0, c->n_slots, c->staging.p, dev_sc(c), c->sm_count, codes,
                                    c->stream));
       }
       {
@@ -468,16 +482,24 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
         AMR_CUDA(launch_bin_fine(c->n_slots, c->staging.p, dev_sc(c), c->stream));
       }
       KernelTimer kt(c, KT_PLACE);
-      AMR_CUDA(launch_place_windows(c->n_slots, c->staging.p, static_cast<unsigned long long*>(c->rec.p),
-                                    c->stream));
+      AMR_CUDA(launch_place_windows(logb, c->n_slots, c->staging.p, static_cast<unsigned long long*>(c->rec.p),
+                                    static_cast<unsigned*>(c->view.p), static_cast<float*>(c->scal.p),
+                                    static_cast<unsigned*>(c->elist.p), dev_sc(c), c->stream));
     } else {
       AMR_CUDA(cudaMemsetAsync(c->rec.p, 0xFF, (size_t)c->n_slots * 8, c->stream));
       KernelTimer kt(c, KT_SCATTER);
-      AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, L,
+      AMR_CUDA(launch_scatter_cells(logb, c->xyz, c->lvl, c->s, n, make_locator(c),
                                     static_cast<unsigned long long*>(c->rec.p), dev_sc(c),
                                     grid_for(c, n, block, 2048 / block), block, c->stream));
     }
-    {
+    const Locator L = make_locator(c);
+    if (binned_ok && !overlap) {   // only the bricks with empty slots are left to resolve
+      KernelTimer kt(c, KT_RESOLVE_EMPTY);
+      AMR_CUDA(launch_resolve_empty(logb, L, static_cast<const unsigned*>(c->elist.p), dev_sc(c),
+                                    static_cast<unsigned*>(c->view.p), c->sm_count * 8, c->stream));
+    } else {   // every slot (and, on request, every occupied slot checked against coarser cells)
+      if (binned_ok)   // the window pass counted the occupied slots already
+        AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->n_occupied, 0, sizeof(unsigned long long), c->stream));
       KernelTimer kt(c, KT_RESOLVE);
       AMR_CUDA(launch_resolve_views(logb, L, static_cast<unsigned*>(c->view.p), static_cast<float*>(c->scal.p),
                                     c->n_slots, overlap, dev_sc(c), grid_for(c, c->n_slots, block, 2048 / block),
@@ -517,7 +539,19 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   return AMR_OK;
 }
 
-int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
+namespace {
+int dual_cells_owned(amr_ctx* c, int x0, int x1, int64_t* n_dual);
+}
+
+int amr_dual_cells(amr_ctx* c, int64_t* n_dual) { return dual_cells_owned(c, INT_MIN, INT_MAX, n_dual); }
+
+int amr_dual_cells_owned(amr_ctx* c, int32_t x_begin, int32_t x_end, int64_t* n_dual) {
+  if (x_end < x_begin) return AMR_ERR_INVALID_ARG;
+  return dual_cells_owned(c, x_begin, x_end, n_dual);
+}
+
+namespace {
+int dual_cells_owned(amr_ctx* c, int x0, int x1, int64_t* n_dual) {
   if (!c || !n_dual) return AMR_ERR_INVALID_ARG;
   if (c->stage < 2) return AMR_ERR_STATE;
   AMR_CUDA(cudaSetDevice(c->device));
@@ -532,7 +566,7 @@ int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
       KernelTimer kt(c, KT_DUAL);
       AMR_CUDA(launch_dual_cells(c->logb, make_locator(c), static_cast<const int*>(c->nbr.p),
                                  static_cast<const int*>(c->border.p), c->n_bricks, static_cast<uint4*>(c->duals.p),
-                                 c->dual_cap, dev_sc(c), c->stream));
+                                 c->dual_cap, dev_sc(c), c->stream, x0, x1));
     }
     AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_dual, &dev_sc(c)->n_dual, sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, c->stream));
@@ -540,6 +574,7 @@ int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
     const long long nd = (long long)c->host_sc->n_dual;
     if (nd <= c->dual_cap) {
       c->n_dual = nd;
+      AMR_TRY(ensure(c->bwork, batch_workspace_bytes((nd + kBTile - 1) / kBTile * kMaxIso)));
       c->stage = 3;
       *n_dual = nd;
       return AMR_OK;
@@ -548,6 +583,7 @@ int amr_dual_cells(amr_ctx* c, int64_t* n_dual) {
   }
   return AMR_ERR_CUDA;
 }
+}  // namespace
 
 int amr_dual_cells_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t* n_dual, int64_t* n_tris,
                        int flags) {
@@ -586,6 +622,7 @@ int amr_dual_cells_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t*
     }
     const long long nt = (long long)c->host_sc->n_tri[0];
     c->n_dual = nd;
+    AMR_TRY(ensure(c->bwork, batch_workspace_bytes((nd + kBTile - 1) / kBTile * kMaxIso)));
     c->stage = 3;
     *n_dual = nd;
     *n_tris = nt;
@@ -636,12 +673,11 @@ int amr_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t* n_tris, in
   {
     KernelTimer kt(c, KT_MC);
     AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), c->n_dual, iso, dst,
-                       cap, counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream));
+                       cap, counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8),
+                       c->stream));
   }
-  AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], counter, sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, c->stream));
-  AMR_CUDA(cudaStreamSynchronize(c->stream));
-  const long long nt = (long long)c->host_sc->n_tri[0];
+  long long nt = 0;
+  AMR_TRY(mc_result(c, counter, &nt));
   *n_tris = nt;
   if (flags & AMR_HOST_PTRS) {
     AMR_TRY(deliver(c, tris, dst, (size_t)std::min<long long>(nt, cap) * 36, flags));
@@ -668,16 +704,16 @@ int amr_iso_tagged(amr_ctx* c, float iso, float* tris, int64_t* tri_dual, int64_
   if (cap > 0) {   // without an output there is nothing to tag: count only
     KernelTimer kt(c, KT_MC_TAGGED);
     AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), c->n_dual, iso, dst, cap,
-                       counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream, dtag));
+                       counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream,
+                       dtag));
   } else {
     KernelTimer kt(c, KT_MC);
     AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), c->n_dual, iso, nullptr,
-                       0, counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream));
+                       0, counter, nullptr, nullptr, c->mc, grid_for(c, c->n_dual, 256, 8),
+                       c->stream));
   }
-  AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], counter, sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, c->stream));
-  AMR_CUDA(cudaStreamSynchronize(c->stream));
-  const long long nt = (long long)c->host_sc->n_tri[0];
+  long long nt = 0;
+  AMR_TRY(mc_result(c, counter, &nt));
   *n_tris = nt;
   if (host && cap > 0) {
     const size_t w = (size_t)std::min<long long>(nt, cap);
@@ -707,12 +743,10 @@ int amr_iso_indexed(amr_ctx* c, float iso, float* vtx, int64_t vcap, int32_t* tr
     {
       KernelTimer kt(c, KT_MC_KEYS);
       AMR_CUDA(launch_mc_keys(c->logb, L, du, c->n_dual, iso, static_cast<unsigned long long*>(c->tkeys.p),
-                              c->tkeys_cap, counter, c->mc, grid_for(c, c->n_dual, 256, 8), c->stream));
+                              c->tkeys_cap, counter, c->mc, grid_for(c, c->n_dual, 256, 8),
+                              c->stream));
     }
-    AMR_CUDA(cudaMemcpyAsync(&c->host_sc->n_tri[0], counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                             c->stream));
-    AMR_CUDA(cudaStreamSynchronize(c->stream));
-    nt = (long long)c->host_sc->n_tri[0];
+    AMR_TRY(mc_result(c, counter, &nt));
     if (nt <= c->tkeys_cap) break;
     kcap = nt;
   }
@@ -843,13 +877,24 @@ int amr_iso_cases(amr_ctx* c, float iso, uint8_t* cases, uint8_t* ntri, int flag
   {
     KernelTimer kt(c, KT_MC_CASES);
     AMR_CUDA(launch_mc(c->logb, make_locator(c), static_cast<const uint4*>(c->duals.p), nd, iso, nullptr, 0,
-                       nullptr, dc, dn, c->mc, grid_for(c, nd, 256, 8), c->stream));
+                       &dev_sc(c)->n_tri[0], dc, dn, c->mc, grid_for(c, nd, 256, 8), c->stream));
   }
+  long long unused = 0;
+  AMR_TRY(mc_result(c, &dev_sc(c)->n_tri[0], &unused));
   if (cases) AMR_TRY(deliver(c, cases, dc, (size_t)nd, flags));
   if (ntri) AMR_TRY(deliver(c, ntri, dn, (size_t)nd, flags));
   AMR_CUDA(cudaStreamSynchronize(c->stream));
   return AMR_OK;
 }
+
+namespace {
+BatchTable single_job(amr_ctx* c, int n_iso) {
+  BatchTable T;
+  batch_add_job(T, static_cast<const uint4*>(c->duals.p), static_cast<const float*>(c->scal.p),
+                static_cast<const int4*>(c->bricks.p), c->n_dual, c->logb, n_iso);
+  return T;
+}
+}  // namespace
 
 int amr_iso_batch(amr_ctx* c, const float* isos, int n_iso, float* tris, int64_t cap, int64_t* offsets,
                   int flags) {
@@ -857,44 +902,35 @@ int amr_iso_batch(amr_ctx* c, const float* isos, int n_iso, float* tris, int64_t
     return AMR_ERR_INVALID_ARG;
   if (c->stage < 3) return AMR_ERR_STATE;
   AMR_CUDA(cudaSetDevice(c->device));
-  const long long nd = c->n_dual;
   AMR_TRY(ensure(c->iso_buf, sizeof(float) * kMaxIso));
   AMR_TRY(ensure(c->seg_buf, sizeof(long long) * (kMaxIso + 1)));
   float* d_iso = static_cast<float*>(c->iso_buf.p);
+  long long* d_off = static_cast<long long*>(c->seg_buf.p);
   AMR_CUDA(cudaMemcpyAsync(d_iso, isos, sizeof(float) * n_iso, cudaMemcpyHostToDevice, c->stream));
-  AMR_CUDA(cudaMemsetAsync(dev_sc(c)->n_tri, 0, sizeof(unsigned long long) * kMaxIso, c->stream));
-  const Locator L = make_locator(c);
-  const uint4* du = static_cast<const uint4*>(c->duals.p);
+  const BatchTable T = single_job(c, n_iso);
   const int grid = c->sm_count * 8;
   {
     KernelTimer kt(c, KT_BATCH_COUNT);
-    AMR_CUDA(launch_mc_batch_count(c->logb, L, du, nd, d_iso, n_iso, dev_sc(c), c->mc,
-                                   grid_for(c, nd, 256, 8), c->stream));
+    AMR_CUDA(launch_batch_count(T, d_iso, c->bwork.p, c->mc, grid, c->stream));
   }
-  AMR_CUDA(cudaMemcpyAsync(c->host_sc->n_tri, dev_sc(c)->n_tri, sizeof(unsigned long long) * n_iso,
-                           cudaMemcpyDeviceToHost, c->stream));
+  {
+    KernelTimer kt(c, KT_BATCH_SCAN);
+    AMR_CUDA(launch_batch_scan(T, c->bwork.p, d_off, c->stream));
+  }
+  AMR_CUDA(cudaMemcpyAsync(c->host_sc->n_tri, d_off, sizeof(long long) * (n_iso + 1), cudaMemcpyDeviceToHost,
+                           c->stream));
   AMR_CUDA(cudaStreamSynchronize(c->stream));
-  long long run = 0;
-  for (int k = 0; k < n_iso; ++k) {
-    offsets[k] = run;
-    run += (long long)c->host_sc->n_tri[k];
-  }
-  offsets[n_iso] = run;
+  for (int k = 0; k <= n_iso; ++k) offsets[k] = (int64_t)c->host_sc->n_tri[k];
+  const long long run = offsets[n_iso];
   if (run > cap) return AMR_ERR_CAPACITY;
   float* dst = tris;
   if (flags & AMR_HOST_PTRS) {
     AMR_TRY(ensure(c->stage_buf, (size_t)std::max<long long>(run, 1) * 36));
     dst = static_cast<float*>(c->stage_buf.p);
   }
-  long long* d_off = static_cast<long long*>(c->seg_buf.p);
-  AMR_CUDA(cudaMemcpyAsync(d_off, offsets, sizeof(long long) * (n_iso + 1), cudaMemcpyHostToDevice,
-                           c->stream));
-  AMR_CUDA(cudaMemsetAsync(dev_sc(c)->n_tri, 0, sizeof(unsigned long long) * kMaxIso, c->stream));
-  AMR_CUDA(cudaMemsetAsync(&dev_sc(c)->tile, 0, sizeof(unsigned long long), c->stream));
   {
     KernelTimer kt(c, KT_BATCH_EMIT);
-    AMR_CUDA(launch_mc_batch_emit(c->logb, L, du, nd, d_iso, n_iso, dst, d_off, run, dev_sc(c), c->mc,
-                                  grid, 4096, c->stream));
+    AMR_CUDA(launch_batch_emit(T, d_iso, c->bwork.p, d_off, dst, run, c->mc, grid, c->stream));
   }
   if (flags & AMR_HOST_PTRS) AMR_TRY(deliver(c, tris, dst, (size_t)run * 36, flags));
   AMR_CUDA(cudaStreamSynchronize(c->stream));
@@ -906,22 +942,64 @@ int amr_iso_batch_async(amr_ctx* c, const float* d_isos, int n_iso, float* tris,
   if (!c || !d_isos || !d_offsets || n_iso < 1 || n_iso > kMaxIso || cap < 0 || (cap > 0 && !tris))
     return AMR_ERR_INVALID_ARG;
   if (c->stage < 3) return AMR_ERR_STATE;
-  const long long nd = c->n_dual;
-  const Locator L = make_locator(c);
-  const uint4* du = static_cast<const uint4*>(c->duals.p);
-  AMR_CUDA(cudaMemsetAsync(dev_sc(c)->n_tri, 0, sizeof(unsigned long long) * kMaxIso, c->stream));
+  const BatchTable T = single_job(c, n_iso);
+  long long* off = reinterpret_cast<long long*>(d_offsets);
+  const int grid = c->sm_count * 8;
   {
     KernelTimer kt(c, KT_BATCH_COUNT);
-    AMR_CUDA(launch_mc_batch_count(c->logb, L, du, nd, d_isos, n_iso, dev_sc(c), c->mc,
-                                   grid_for(c, nd, 256, 8), c->stream));
+    AMR_CUDA(launch_batch_count(T, d_isos, c->bwork.p, c->mc, grid, c->stream));
   }
-  AMR_CUDA(launch_batch_offsets(dev_sc(c), n_iso, reinterpret_cast<long long*>(d_offsets), c->stream));
+  {
+    KernelTimer kt(c, KT_BATCH_SCAN);
+    AMR_CUDA(launch_batch_scan(T, c->bwork.p, off, c->stream));
+  }
   {
     KernelTimer kt(c, KT_BATCH_EMIT);
-    AMR_CUDA(launch_mc_batch_emit(c->logb, L, du, nd, d_isos, n_iso, tris,
-                                  reinterpret_cast<const long long*>(d_offsets), cap, dev_sc(c), c->mc,
-                                  c->sm_count * 8, 4096, c->stream));
+    AMR_CUDA(launch_batch_emit(T, d_isos, c->bwork.p, off, tris, cap, c->mc, grid, c->stream));
   }
+  return AMR_OK;
+}
+
+namespace {
+// The batch table of a multi-data-set batch; AMR_OK or the reason it is refused.
+int multi_table(const amr_iso_job* jobs, int n_jobs, BatchTable* T) {
+  if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs) return AMR_ERR_INVALID_ARG;
+  int dev = -1;
+  for (int j = 0; j < n_jobs; ++j) {
+    amr_ctx* c = jobs[j].ctx;
+    if (!c || jobs[j].n_iso < 1) return AMR_ERR_INVALID_ARG;
+    if (T->n_q + jobs[j].n_iso > kMaxIso) return AMR_ERR_INVALID_ARG;
+    if (c->stage < 3) return AMR_ERR_STATE;
+    if (dev >= 0 && c->device != dev) return AMR_ERR_INVALID_ARG;
+    dev = c->device;
+    batch_add_job(*T, static_cast<const uint4*>(c->duals.p), static_cast<const float*>(c->scal.p),
+                  static_cast<const int4*>(c->bricks.p), c->n_dual, c->logb, jobs[j].n_iso);
+  }
+  return AMR_OK;
+}
+}  // namespace
+
+int64_t amr_iso_multi_workspace(const amr_iso_job* jobs, int n_jobs) {
+  BatchTable T;
+  const int rc = multi_table(jobs, n_jobs, &T);
+  if (rc != AMR_OK) return rc;
+  return (int64_t)batch_workspace_bytes(T.n_counters);
+}
+
+int amr_iso_multi_async(const amr_iso_job* jobs, int n_jobs, const float* d_isos, float* tris, int64_t cap,
+                        int64_t* d_offsets, void* workspace, int64_t workspace_bytes, void* cuda_stream) {
+  BatchTable T;
+  AMR_TRY(multi_table(jobs, n_jobs, &T));
+  if (!d_isos || !d_offsets || !workspace || cap < 0 || (cap > 0 && !tris) ||
+      workspace_bytes < (int64_t)batch_workspace_bytes(T.n_counters))
+    return AMR_ERR_INVALID_ARG;
+  amr_ctx* c0 = jobs[0].ctx;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  long long* off = reinterpret_cast<long long*>(d_offsets);
+  const int grid = c0->sm_count * 8;
+  AMR_CUDA(launch_batch_count(T, d_isos, workspace, c0->mc, grid, st));
+  AMR_CUDA(launch_batch_scan(T, workspace, off, st));
+  AMR_CUDA(launch_batch_emit(T, d_isos, workspace, off, tris, cap, c0->mc, grid, st));
   return AMR_OK;
 }
 
@@ -936,8 +1014,9 @@ int amr_get_info(amr_ctx* c, amr_info* info) {
   info->placement = c->placement;
   info->reserved = 0;
   const DevBuf* bufs[] = {&c->own_xyz, &c->own_lvl, &c->own_s, &c->htab, &c->bricks,
-                          &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes, &c->duals,
-                          &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->tkeys, &c->wtab,
+                          &c->rec, &c->scal, &c->view, &c->nbr, &c->staging, &c->codes,
+                          &c->elist, &c->duals,
+                          &c->scratch, &c->stage_buf, &c->iso_buf, &c->seg_buf, &c->bwork, &c->tkeys, &c->wtab,
                           &c->ostage, &c->border, &c->bcount};
   long long total = 0;
   for (const DevBuf* b : bufs) total += (long long)held(*b);

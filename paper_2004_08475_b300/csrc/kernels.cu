@@ -22,6 +22,7 @@
 // coarser level then holds the answer, because an aligned level-l brick lies
 // inside one aligned brick of every coarser level.
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -122,11 +123,18 @@ constexpr int kUnroll = 4;   // cells per lane per trip of the cell-parallel loo
 
 // Pass 1 over the cells: validate corners and levels, take the bounding box
 // and the deepest level, and insert every cell's brick key into the hash
-// table (scalars are checked in pass 2). The CAS
-// winner of a key numbers the brick and records its corner and level. Each
-// lane takes kUnroll cells per trip, loads and first probes hoisted, so that
-// their memory latencies overlap. Lanes holding the same key simply both
-// find it (or race on one CAS, which one of them wins).
+// table (scalars are checked in pass 2). The CAS winner of a key numbers the
+// brick and records its corner and level. Each lane takes kUnroll cells per
+// trip, loads and first probes hoisted, so that their memory latencies
+// overlap; the first probe reads the home sector's two entries whole (key
+// and brick index). Lanes holding the same key simply both find it (or race
+// on one CAS, which one of them wins).
+// codes (binned placement): per cell its slot (brick index << 3 LOGB | its
+// Morton index in the brick) when the brick's index was already readable,
+// else kCodeEntry | its brick's table entry << 3 LOGB | Morton index (the
+// winner of that brick had not stored the index yet; k_bin_coarse reads it).
+constexpr unsigned kCodeEntry = 0x80000000u;
+
 template <int LOGB>
 __global__ void __launch_bounds__(1024) k_insert_bricks(
     const int* __restrict__ xyz, const unsigned char* __restrict__ lvl,
@@ -136,6 +144,7 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int hshift = 64 - __popcll(hmask);
   int lo0 = INT_MAX, lo1 = INT_MAX, lo2 = INT_MAX;
   int hi0 = INT_MIN, hi1 = INT_MIN, hi2 = INT_MIN;
   int ml = 0;
@@ -158,75 +167,81 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
         l[u] = __ldcs(lvl + i);
       }
     }
-    unsigned long long key[kUnroll], h[kUnroll], cur[kUnroll], cur1[kUnroll];
-    unsigned loc[kUnroll];
-    bool lead[kUnroll];
+    unsigned long long key[kUnroll];
+    ulonglong2 e0[kUnroll];
+    unsigned long long cur1[kUnroll];
+    unsigned h[kUnroll], loc[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       key[u] = kEmptyKey;
       loc[u] = 0;
+      h[u] = 0;
       if (l[u] >= 0) {
         if (l[u] > kMaxLevel) {
           err |= ERR_RANGE;
         } else if ((x[u] | y[u] | z[u]) & ((1 << l[u]) - 1)) {
           err |= ERR_UNALIGNED;
+        } else if (max(max(x[u], y[u]), z[u]) > (1 << 30) || min(min(x[u], y[u]), z[u]) < -(1 << 30)) {
+          err |= ERR_RANGE;   // corners beyond +-2^30 (so that x + w stays below 2^31)
         } else {
-          const long long w = 1ll << l[u];
+          const int w = 1 << l[u];
           lo0 = min(lo0, x[u]);
           lo1 = min(lo1, y[u]);
           lo2 = min(lo2, z[u]);
-          hi0 = max(hi0, (int)min((long long)x[u] + w, (long long)INT_MAX));
-          hi1 = max(hi1, (int)min((long long)y[u] + w, (long long)INT_MAX));
-          hi2 = max(hi2, (int)min((long long)z[u] + w, (long long)INT_MAX));
+          hi0 = max(hi0, x[u] + w);
+          hi1 = max(hi1, y[u] + w);
+          hi2 = max(hi2, z[u] + w);
           ml = max(ml, l[u]);
           key[u] = brick_key<LOGB>(x[u], y[u], z[u], l[u]);
           loc[u] = local_index<LOGB>(x[u], y[u], z[u], l[u]);
+          h[u] = (unsigned)((key[u] * 0x9E3779B97F4A7C15ull) >> hshift) & ~1u;   // home_of
         }
       }
-      lead[u] = key[u] != kEmptyKey;
-      h[u] = home_of(key[u], hmask);
-      cur[u] = lead[u] ? __ldcg(&htab[h[u]].x) : 0ull;   // independent first probes: the home sector
-      cur1[u] = lead[u] ? __ldcg(&htab[h[u] + 1].x) : 0ull;
+      // independent first probes: the home sector (entry h whole, entry h + 1's key)
+      e0[u] = key[u] != kEmptyKey ? __ldcg(htab + h[u]) : make_ulonglong2(0ull, 0ull);
+      cur1[u] = key[u] != kEmptyKey ? __ldcg(&htab[h[u] + 1].x) : 0ull;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const bool home = cur[u] == key[u] || cur1[u] == key[u];
-      if (codes && lead[u] && home) {   // found in its home sector
-        const long long i = base + u * 32 + lane;
-        const unsigned e = (unsigned)h[u] + (cur[u] == key[u] ? 0u : 1u);
-        __stcs(codes + i, (e << (3 * LOGB)) | loc[u]);
-      }
-      if (!lead[u] || home) continue;
-      unsigned long long hh = h[u];
-      bool done = false;
-      for (unsigned long long p = 0; p < limit; ++p) {
-        const unsigned long long c = p == 0 ? cur[u] : __ldcg(&htab[hh].x);
-        if (c == key[u]) { done = true; break; }
-        if (c == kEmptyKey) {
-          const unsigned long long prev = atomicCAS(&htab[hh].x, kEmptyKey, key[u]);
-          if (prev == kEmptyKey) {
-            const unsigned long long bi = atomicAdd(&sc->n_bricks, 1ull);
-            htab[hh].y = bi;
-            if (bi < brick_limit) {   // bricks[] holds brick_limit entries; the cell is read again
-              const long long i = base + u * 32 + lane;
-              const int lv = lvl[i];
-              const int m = ~((1 << (lv + LOGB)) - 1);
-              bricks[bi] = make_int4(xyz[3 * i] & m, xyz[3 * i + 1] & m, xyz[3 * i + 2] & m, lv);
-            } else {
-              atomicOr(&sc->err, (unsigned)ERR_HASH_FULL);
+      if (key[u] == kEmptyKey) continue;
+      const long long i = base + u * 32 + lane;
+      unsigned code;
+      if (e0[u].x == key[u]) {   // at home, the common case: the brick index came with the key
+        code = e0[u].y != kEmptyKey ? ((unsigned)e0[u].y << (3 * LOGB)) | loc[u]
+                                    : kCodeEntry | (h[u] << (3 * LOGB)) | loc[u];
+      } else if (cur1[u] == key[u]) {
+        code = kCodeEntry | ((h[u] + 1) << (3 * LOGB)) | loc[u];
+      } else {
+        unsigned long long hh = h[u];
+        bool done = false;
+        code = kReject;
+        for (unsigned long long p = 0; p < limit; ++p) {
+          const unsigned long long c = p == 0 ? e0[u].x : (p == 1 ? cur1[u] : __ldcg(&htab[hh].x));
+          if (c == key[u]) { done = true; break; }
+          if (c == kEmptyKey) {
+            const unsigned long long prev = atomicCAS(&htab[hh].x, kEmptyKey, key[u]);
+            if (prev == kEmptyKey) {
+              const unsigned long long bi = atomicAdd(&sc->n_bricks, 1ull);
+              htab[hh].y = bi;
+              if (bi < brick_limit) {   // bricks[] holds brick_limit entries; the cell is read again
+                const int lv = lvl[i];
+                const int m = ~((1 << (lv + LOGB)) - 1);
+                bricks[bi] = make_int4(xyz[3 * i] & m, xyz[3 * i + 1] & m, xyz[3 * i + 2] & m, lv);
+                code = ((unsigned)bi << (3 * LOGB)) | loc[u];
+              } else {
+                atomicOr(&sc->err, (unsigned)ERR_HASH_FULL);
+              }
+              done = true;
+              break;
             }
-            done = true;
-            break;
+            if (prev == key[u]) { done = true; break; }
           }
-          if (prev == key[u]) { done = true; break; }
+          hh = (hh + 1) & hmask;
         }
-        hh = (hh + 1) & hmask;
+        if (!done) err |= ERR_HASH_FULL;
+        else if (code == kReject) code = kCodeEntry | ((unsigned)hh << (3 * LOGB)) | loc[u];
       }
-      if (!done) err |= ERR_HASH_FULL;
-      if (codes && done) {   // the entry that holds the key stays put (no deletions)
-        const long long i = base + u * 32 + lane;
-        __stcs(codes + i, ((unsigned)hh << (3 * LOGB)) | loc[u]);
-      }
+      if (codes) __stcs(codes + i, code);
     }
   }
   // block reduction, then one set of atomics per block
@@ -412,8 +427,8 @@ __device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gb
   return total;
 }
 
-// A cell's slot is one table read away: its code (from k_insert_bricks)
-// holds the table entry of its brick << 3 LOGB | its Morton index there.
+// A cell's slot is its code (from k_insert_bricks), or one table read away
+// when the code holds the table entry of its brick instead.
 template <int LOGB>
 __global__ void __launch_bounds__(kCoarseThreads) k_bin_coarse(const float* __restrict__ s, long long n, Locator L,
                                                                int n_coarse, Stage A,
@@ -444,8 +459,11 @@ __global__ void __launch_bounds__(kCoarseThreads) k_bin_coarse(const float* __re
         const float v = __ldcs(s + i);
         if (!isfinite(v)) err |= ERR_NONFINITE;
         val[j] = __float_as_uint(v);
-        const unsigned bi = (unsigned)__ldg(&L.htab[c >> (3 * LOGB)].y);
-        slot[j] = (bi << (3 * LOGB)) | (c & ((1u << (3 * LOGB)) - 1u));
+        slot[j] = c;
+        if (c & kCodeEntry) {   // the brick's index was not stored yet when the cell was inserted
+          const unsigned bi = (unsigned)__ldg(&L.htab[(c & ~kCodeEntry) >> (3 * LOGB)].y);
+          slot[j] = (bi << (3 * LOGB)) | (c & ((1u << (3 * LOGB)) - 1u));
+        }
       }
     }
 #pragma unroll
@@ -544,26 +562,95 @@ __global__ void __launch_bounds__(kFineThreads) k_bin_fine(Stage A, const unsign
   if ((t & 31) == 0 && err) atomicOr(&sc->err, err);
 }
 
-// One CTA per window of kWinSlots slots.
+// One CTA per window of kWinSlots slots: the records built in shared memory
+// and written whole (empty slots as kEmptyRec), and with them each slot's
+// view (the slot itself where a cell occupies it, else kReject for now) and
+// scalar (0 when empty); counts the occupied slots and lists the bricks that
+// have empty slots (elist, counted by sc->n_elist) for k_resolve_empty.
+template <int LOGB>
 __global__ void __launch_bounds__(kPlaceThreads) k_place_windows(Stage B, const unsigned* __restrict__ win_count,
-                                                                 long long n_slots, unsigned long long* rec) {
+                                                                 long long n_slots, unsigned long long* rec,
+                                                                 unsigned* view, float* scal,
+                                                                 unsigned* __restrict__ elist, Scratch* sc) {
+  constexpr int kBricksPerWin = kWinSlots >> (3 * LOGB);
   extern __shared__ __align__(16) unsigned long long win[];   // [kWinSlots]
+  __shared__ unsigned char holes[kBricksPerWin];
+  __shared__ unsigned occ_w[kPlaceThreads / 32];
   const int t = threadIdx.x;
   const long long w0 = (long long)blockIdx.x << kWinShift;
   for (int k = t; k < kWinSlots; k += kPlaceThreads) win[k] = kEmptyRec;
+  for (int k = t; k < kBricksPerWin; k += kPlaceThreads) holes[k] = 0;
   __syncthreads();
   const unsigned cnt = min(__ldg(win_count + blockIdx.x), (unsigned)kWinSlots);
   for (unsigned e = t; e < cnt; e += kPlaceThreads) {
     const unsigned sl = __ldcs(B.slot + w0 + e);
-    win[sl & (kWinSlots - 1)] =
-        ((unsigned long long)__ldcs(B.val + w0 + e) << 32) | __ldcs(B.idx + w0 + e);
+    win[sl & (kWinSlots - 1)] = ((unsigned long long)__ldcs(B.val + w0 + e) << 32) | __ldcs(B.idx + w0 + e);
   }
   __syncthreads();
   // n_slots is a multiple of the brick size (>= 64), so windows end on pairs
   const long long m = min((long long)kWinSlots, n_slots - w0);
   ulonglong2* dst = reinterpret_cast<ulonglong2*>(rec + w0);
+  uint2* vdst = reinterpret_cast<uint2*>(view + w0);
+  float2* sdst = reinterpret_cast<float2*>(scal + w0);
   const ulonglong2* srcw = reinterpret_cast<const ulonglong2*>(win);
-  for (long long k = t; k < m / 2; k += kPlaceThreads) dst[k] = srcw[k];
+  unsigned occ = 0;
+  for (long long k = t; k < m / 2; k += kPlaceThreads) {
+    const ulonglong2 r = srcw[k];
+    dst[k] = r;
+    const bool o0 = r.x != kEmptyRec, o1 = r.y != kEmptyRec;
+    const unsigned s0 = (unsigned)(w0 + 2 * k);
+    vdst[k] = make_uint2(o0 ? s0 : kReject, o1 ? s0 + 1 : kReject);
+    sdst[k] = make_float2(o0 ? __uint_as_float((unsigned)(r.x >> 32)) : 0.f,
+                          o1 ? __uint_as_float((unsigned)(r.y >> 32)) : 0.f);
+    occ += (o0 ? 1u : 0u) + (o1 ? 1u : 0u);
+    if (!(o0 && o1)) holes[(2 * k) >> (3 * LOGB)] = 1;
+  }
+  occ = __reduce_add_sync(kFull, occ);
+  if ((t & 31) == 0) occ_w[t >> 5] = occ;
+  __syncthreads();
+  if (t < 32) {
+    unsigned a = t < kPlaceThreads / 32 ? occ_w[t] : 0u;
+    a = __reduce_add_sync(kFull, a);
+    if (t == 0 && a) atomicAdd(&sc->n_occupied, (unsigned long long)a);
+    // bricks of this window with empty slots, one reservation per window
+    const int nb = (int)(m >> (3 * LOGB));
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+      const bool h = b0 + t < nb && holes[b0 + t];
+      const unsigned bal = __ballot_sync(kFull, h);
+      if (!bal) continue;
+      unsigned long long base = 0;
+      if (t == 0) base = atomicAdd(&sc->n_elist, (unsigned long long)__popc(bal));
+      base = __shfl_sync(kFull, base, 0);
+      if (h) elist[base + __popc(bal & ((1u << t) - 1u))] = (unsigned)((w0 >> (3 * LOGB)) + b0 + t);
+    }
+  }
+}
+
+// Pass over the bricks listed by k_place_windows: each of their empty slots
+// resolved to the actual cell containing its logical cell - the first
+// occupied slot at a coarser level (a slot is occupied iff its view is
+// itself), else kReject (finer cells or a hole). The list's length is read
+// on the device (sc->n_elist).
+template <int LOGB>
+__global__ void __launch_bounds__(256) k_resolve_empty(Locator L, const unsigned* __restrict__ elist,
+                                                       const Scratch* sc, unsigned* view) {
+  constexpr int kB3 = 1 << (3 * LOGB);
+  const long long total = (long long)__ldcg(&sc->n_elist) * kB3;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const unsigned slot = (__ldg(elist + (i >> (3 * LOGB))) << (3 * LOGB)) | (unsigned)(i & (kB3 - 1));
+    if (view[slot] != kReject) continue;   // occupied: view is the slot itself
+    const int4 c = slot_cell<LOGB>(L.bricks, slot);
+    for (int lv = c.w + 1; lv < L.levels; ++lv) {
+      const int bj = find_brick(L, brick_key<LOGB>(c.x, c.y, c.z, lv));
+      if (bj < 0) continue;
+      const unsigned s2 = ((unsigned)bj << (3 * LOGB)) | local_index<LOGB>(c.x, c.y, c.z, lv);
+      if (view[s2] == s2) {   // an empty slot's view is never itself, whether resolved yet or not
+        view[slot] = s2;
+        break;
+      }
+    }
+  }
 }
 
 // Pass over the slots: resolve every logical cell of every brick to the
@@ -901,11 +988,15 @@ struct DualShape {
 // extraction kernel): the region's scalars are staged in shared memory too,
 // and the kept triangles are appended with one atomic per warp - the same
 // triangles, bit for bit, as k_mc over the resident dual list.
+//
+// Only cells whose lower corner's x lies in [own_x0, own_x1) emit (the
+// owner slab of a sharded data set; the whole range otherwise): every other
+// cell still takes part in its neighbours' rules.
 template <int LOGB, bool ISO>
 __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     Locator L, const int* __restrict__ nbr, const int* __restrict__ order, long long n_bricks,
     uint4* __restrict__ duals, long long cap, Scratch* sc, float iso, float* __restrict__ tris, long long tri_cap,
-    const __grid_constant__ McConst mc) {
+    int own_x0, int own_x1, const __grid_constant__ McConst mc) {
   constexpr int B = 1 << LOGB;
   constexpr int R = B + 2;
   constexpr int NT = DualShape<LOGB>::kThreads;
@@ -961,9 +1052,6 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
       level_only = level_only && mine[j];
       const int r = c0[j] + 1 + RS + PS;
       rv[r] = mine[j] ? (v | kSame) : v;
-      if (v != kReject)
-        atomicOr(&rmask[(py[j] + 1) + R * (pz[j] + 1)],
-                 (1u << (px[j] + 1)) | ((mine[j] ? 1u : 0u) << (16 + px[j] + 1)));
     }
     const unsigned* halo = halo_list<LOGB>();
     for (int k = t; k < HaloList<LOGB>::kCount; k += NT) {   // the one-cell halo
@@ -985,12 +1073,28 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
         same = lv == l && v == s2;
       }
       rv[rx + RS * ry + PS * rz] = same ? (v | kSame) : v;
-      if (v != kReject) atomicOr(&rmask[ry + R * rz], (1u << rx) | ((same ? 1u : 0u) << (16 + rx)));
       level_only = level_only && same;
     }
     // A region made only of level-l cells leaves each cell exactly one dual:
-    // the one it is the lowest vertex of (d = 7); rules 1-3 need not run.
+    // the one it is the lowest vertex of (d = 7); rules 1-3 need not run,
+    // and the row masks are built only for the other bricks.
     const bool uniform = __syncthreads_and(level_only) != 0;
+    if (!uniform) {
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const unsigned v = rv[c0[j] + 1 + RS + PS];
+        if (v != kReject)
+          atomicOr(&rmask[(py[j] + 1) + R * (pz[j] + 1)],
+                   (1u << (px[j] + 1)) | ((v & kSame) ? 1u << (16 + px[j] + 1) : 0u));
+      }
+      for (int k = t; k < HaloList<LOGB>::kCount; k += NT) {
+        const unsigned h = __ldg(halo + k);
+        const int rx = (int)(h & 15u), ry = (int)((h >> 4) & 15u), rz = (int)((h >> 8) & 15u);
+        const unsigned v = rv[rx + RS * ry + PS * rz];
+        if (v != kReject) atomicOr(&rmask[ry + R * rz], (1u << rx) | ((v & kSame) ? 1u << (16 + rx) : 0u));
+      }
+      __syncthreads();
+    }
     if (ISO) {
       for (int q = t; q < NR; q += NT) {
         const int r = q % R + RS * ((q / R) % R) + PS * (q / (R * R));
@@ -1005,6 +1109,8 @@ __global__ void __launch_bounds__(DualShape<LOGB>::kThreads) k_dual_cells(
     for (int j = 0; j < CPT; ++j) {
       emit[j] = 0;
       if (!mine[j]) continue;   // the slot holds no level-l cell
+      const int cx = b.x + (px[j] << l);
+      if (cx < own_x0 || cx >= own_x1) continue;   // owned by another slab
       if (uniform) {
         emit[j] = 0x80u;
         cnt += 1u << (16 * j);
@@ -1344,8 +1450,9 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
 // a hash table (16-byte entries {key, vertex index}, Fibonacci home, linear
 // probing); the thread whose CAS places a key numbers the vertex (one atomic
 // per warp), computes its position once and records its cells' input
-// indices. A probe run longer than `limit` sets ERR_HASH_FULL (the host
-// rebuilds the table larger).
+// indices. Neighbouring triangles share edges, so a warp's 32 keys repeat:
+// only the first lane holding each distinct key probes. A probe run longer
+// than `limit` sets ERR_HASH_FULL (the host rebuilds the table larger).
 template <int LOGB>
 __global__ void __launch_bounds__(256) k_weld_insert(Locator L, const unsigned long long* __restrict__ tkeys,
                                                      long long n_keys, ulonglong2* wtab, unsigned long long wmask,
@@ -1358,9 +1465,10 @@ __global__ void __launch_bounds__(256) k_weld_insert(Locator L, const unsigned l
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += stride) {
     const bool live = i < n_keys;
     const unsigned long long key = live ? __ldcs(tkeys + i) : kEmptyKey;
+    const unsigned peers = __match_any_sync(kFull, key);   // lanes holding the same key
     bool won = false;
     unsigned long long h = 0;
-    if (live) {
+    if (live && (threadIdx.x & 31) == __ffs(peers) - 1) {
       h = home_of(key, wmask);
       bool done = false;
       for (unsigned long long p = 0; p < limit; ++p) {
@@ -1398,190 +1506,375 @@ __global__ void __launch_bounds__(256) k_weld_insert(Locator L, const unsigned l
 }
 
 // Indexed face set, index pass: each triangle's three keys looked up in the
-// completed table.
+// completed table, once per distinct key of a warp.
 __global__ void __launch_bounds__(256) k_weld_index(const unsigned long long* __restrict__ tkeys, long long n_tri,
                                                     const ulonglong2* __restrict__ wtab, unsigned long long wmask,
                                                     int* __restrict__ tri) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_tri; i += stride) {
-    const unsigned long long key = __ldcs(tkeys + i);
-    unsigned long long h = home_of(key, wmask);
+  const long long nk = (3 * n_tri + 31) & ~31ll;   // whole warps: the lanes share lookups
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += stride) {
+    const bool live = i < 3 * n_tri;
+    const unsigned long long key = live ? __ldcs(tkeys + i) : kEmptyKey;
+    const unsigned peers = __match_any_sync(kFull, key);   // lanes holding the same key
+    const int leader = __ffs(peers) - 1;
     int vid = -1;
-    for (unsigned long long p = 0; p <= wmask; ++p) {   // every key is in the table
-      const ulonglong2 e = __ldg(wtab + h);
-      if (e.x == key) { vid = (int)e.y; break; }
-      if (e.x == kEmptyKey) break;
-      h = (h + 1) & wmask;
+    if (live && (threadIdx.x & 31) == leader) {
+      unsigned long long h = home_of(key, wmask);
+      for (unsigned long long p = 0; p <= wmask; ++p) {   // every key is in the table
+        const ulonglong2 e = __ldg(wtab + h);
+        if (e.x == key) { vid = (int)e.y; break; }
+        if (e.x == kEmptyKey) break;
+        h = (h + 1) & wmask;
+      }
     }
-    tri[i] = vid;
+    vid = __shfl_sync(kFull, vid, leader);
+    if (live) tri[i] = vid;
   }
 }
 
-// Batched iso-values, count pass: per-iso kept-triangle totals, accumulated
-// in shared memory and added to the global counters once per CTA.
-template <int LOGB>
-__global__ void __launch_bounds__(256) k_mc_batch_count(Locator L, const uint4* __restrict__ duals,
-                                                        long long nd, const float* __restrict__ isos,
-                                                        int n_iso, Scratch* sc,
-                                                        const __grid_constant__ McConst mc) {
+// Batched iso-values over one or several resident dual lists (one launch per
+// pass for all of them). The dual lists are cut into tiles of kBTile duals;
+// a job is one data set's dual list with its run of iso-values, and every
+// (job, iso-value) pair owns one output segment. Three passes:
+//   k_batch_count: per tile, the kept triangles of every iso-value of its
+//     job (each dual's vertex slots and scalars read once for all values);
+//   k_batch_scan: per segment, the exclusive prefix over the job's tiles
+//     (each tile's first row inside the segment) and the segment's total;
+//     k_batch_bases: the segments' first rows (the caller's offsets);
+//   k_batch_emit: per tile, the same cases again; each warp reserves its
+//     triangles of one iso-value inside the tile's run of that segment with
+//     a shared-memory atomic and writes them as one coalesced run.
+// No global atomics and no waiting: every tile knows where its triangles go.
+__device__ __forceinline__ int job_of_tile(const BatchTable& T, long long g) {
+  int j = 0;
+  while (j + 1 < T.n_jobs && g >= T.job[j + 1].tile0) ++j;
+  return j;
+}
+
+__device__ __forceinline__ int4 slot_cell_rt(const int4* __restrict__ bricks, unsigned slot, int logb) {
+  return logb == 3 ? slot_cell<3>(bricks, slot) : slot_cell<2>(bricks, slot);
+}
+
+// One dual per lane, 32 per warp step: its vertex slots and scalars, their
+// range, and whether its 8 vertices are 8 different cells.
+struct BatchDual {
+  unsigned v[8];
+  float s[8];
+  float mn, mx;
+  bool live, distinct;
+};
+
+__device__ __forceinline__ void batch_load(const BatchJob& J, long long d, long long d_hi, BatchDual& b) {
+  b.live = d < d_hi;
+  b.distinct = false;
+  b.mn = 3.4e38f;
+  b.mx = -3.4e38f;
+  if (!b.live) return;
+  b.distinct = load_dual(J.duals, d, b.v);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    b.s[e] = __ldg(J.scal + b.v[e]);
+    b.mn = fminf(b.mn, b.s[e]);
+    b.mx = fmaxf(b.mx, b.s[e]);
+  }
+}
+
+// Minimum and maximum of a float over the warp (dead lanes hold +-3.4e38).
+__device__ __forceinline__ float warp_min_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// Kept-triangle mask of the dual at `iso` (0 when no corner crosses); v:
+// its 8 vertex slots (registers or shared memory).
+__device__ __forceinline__ unsigned batch_keep(const BatchDual& b, const unsigned* v, float iso, const McShared& sh,
+                                               unsigned long long ea, unsigned long long eb, int& cas) {
+  cas = 0;
+  if (!b.live || !(b.mx > iso) || b.mn > iso) return 0u;   // case 0 or 255
+#pragma unroll
+  for (int e = 0; e < 8; ++e) cas |= (b.s[e] > iso ? 1 : 0) << e;
+  return kept_of(b.distinct, sh.packed[cas], sh.count[cas], v, ea, eb);
+}
+
+__global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ BatchTable T,
+                                                     const float* __restrict__ isos, unsigned* __restrict__ counts,
+                                                     const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
-  __shared__ unsigned long long cnt_sh[kMaxIso];
+  __shared__ unsigned cnt[kMaxIso];
   __shared__ float iso_sh[kMaxIso];
   load_mc(sh, mc);
-  for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
-    cnt_sh[k] = 0;
-    iso_sh[k] = isos[k];
-  }
-  __syncthreads();
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < nd; d += stride) {
-    unsigned v[8];
-    float sv[8];
-    const bool distinct = load_dual(duals, d, v);
-    float mn = 3.4e38f, mx = -3.4e38f;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      sv[e] = __ldg(L.scal + v[e]);
-      mn = fminf(mn, sv[e]);
-      mx = fmaxf(mx, sv[e]);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long long g = blockIdx.x; g < T.n_tiles; g += gridDim.x) {
+    const BatchJob& J = T.job[job_of_tile(T, g)];
+    const long long t = g - J.tile0;
+    for (int k = threadIdx.x; k < J.n_iso; k += blockDim.x) {
+      cnt[k] = 0;
+      iso_sh[k] = __ldg(isos + J.q0 + k);
     }
-    for (int k = 0; k < n_iso; ++k) {
-      const float iso = iso_sh[k];
-      if (!(mx > iso) || mn > iso) continue;   // case 0 or 255
-      int cas = 0;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) cas |= (sv[e] > iso ? 1 : 0) << e;
-      const unsigned keep = kept_of(distinct, sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
-      if (keep) atomicAdd(&cnt_sh[k], (unsigned long long)__popc(keep));
+    __syncthreads();
+    const long long d_hi = min(J.nd, (t + 1) * kBTile);
+    for (long long base = t * kBTile + 32 * w; base < d_hi; base += 32 * nw) {
+      BatchDual b;
+      batch_load(J, base + lane, d_hi, b);
+      // the warp's scalar range: iso-values outside it cross none of its duals
+      const float lo = warp_min_f(b.mn), hi = warp_max_f(b.mx);
+      for (int k = 0; k < J.n_iso; ++k) {
+        if (!(hi > iso_sh[k]) || lo > iso_sh[k]) continue;   // uniform over the warp
+        int cas;
+        const unsigned keep = batch_keep(b, b.v, iso_sh[k], sh, mc.edge_a, mc.edge_b, cas);
+        const unsigned c = __reduce_add_sync(kFull, (unsigned)__popc(keep));
+        if (lane == 0 && c) atomicAdd(&cnt[k], c);
+      }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < J.n_iso; k += blockDim.x) counts[J.cbase + k * J.tiles + t] = cnt[k];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < n_iso; k += blockDim.x)
-    if (cnt_sh[k]) atomicAdd(&sc->n_tri[k], cnt_sh[k]);
 }
 
-// Batched iso-values, emit pass: a persistent grid pulls tiles of dual cells
-// from a device counter (no waiting on other CTAs); every dual's vertices and
-// scalars are read once and tested against all iso-values; iso k's triangles
-// go to its own segment tris[seg_off[k] ...] through counter n_tri[k]. Per
-// iso-value the warp lists its kept triangles and computes their vertices
-// lane-parallel into a stage written as one coalesced run, as in k_mc.
-template <int LOGB>
-__global__ void __launch_bounds__(256) k_mc_batch_emit(Locator L, const uint4* __restrict__ duals,
-                                                       long long nd, const float* __restrict__ isos,
-                                                       int n_iso, float* __restrict__ tris,
-                                                       const long long* __restrict__ seg_off, long long total_cap,
-                                                       Scratch* sc, long long tile,
-                                                       const __grid_constant__ McConst mc) {
+// One CTA per segment: rel[...] = exclusive prefix of the segment's tile
+// counts, totals[q] = their sum.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+__global__ void __launch_bounds__(kScanThreads) k_batch_scan(const __grid_constant__ BatchTable T,
+                                                            const unsigned* __restrict__ counts,
+                                                            long long* __restrict__ rel, long long* totals) {
+  __shared__ long long ws[kScanThreads / 32 + 1];
+  const int q = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int j = 0;
+  while (j + 1 < T.n_jobs && q >= T.job[j + 1].q0) ++j;
+  const BatchJob& J = T.job[j];
+  const long long n = J.tiles;
+  const unsigned* c = counts + J.cbase + (long long)(q - J.q0) * n;
+  long long* r = rel + J.cbase + (long long)(q - J.q0) * n;
+  long long running = 0;
+  for (long long c0 = 0; c0 < n; c0 += (long long)kScanThreads * kScanPer) {
+    unsigned v[kScanPer];
+    long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      const long long i = c0 + (long long)t * kScanPer + k;
+      v[k] = i < n ? c[i] : 0u;
+      sum += v[k];
+    }
+    long long incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const long long x = ws[lane];
+      long long cc = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, cc, o);
+        if (lane >= o) cc += y;
+      }
+      ws[lane] = cc - x;
+      if (lane == 31) ws[32] = cc;
+    }
+    __syncthreads();
+    long long ex = running + ws[w] + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      const long long i = c0 + (long long)t * kScanPer + k;
+      if (i < n) r[i] = ex;
+      ex += v[k];
+    }
+    running += ws[32];
+    __syncthreads();
+  }
+  if (t == 0) totals[q] = running;
+}
+
+// off[q] = first row of segment q (exclusive prefix of the totals),
+// off[n_q] = all rows. One thread.
+__global__ void k_batch_bases(int n_q, const long long* totals, long long* off) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long run = 0;
+  for (int q = 0; q < n_q; ++q) {
+    off[q] = run;
+    run += totals[q];
+  }
+  off[n_q] = run;
+}
+
+// Per dual of the emit pass (one per lane of a warp step), computed once for
+// all iso-values: each vertex cell's centre (the fp32 operations of
+// edge_vertex) and scalar, and per hexahedron edge whether its endpoints
+// swap (the upper corner's cell lies lower in (z, y, x) order).
+struct BatchVerts {
+  float4 c[8];        // centre x, y, z and scalar of vertex e
+  unsigned v[8];      // vertex slots
+  unsigned swap;      // bit k: edge k's vertex b comes first
+  unsigned pad[3];
+};
+constexpr int kBatchStage = 64;   // triangles a warp stages per step and iso-value
+
+__device__ __forceinline__ float3 batch_vertex(const BatchVerts& d, int k, unsigned long long ea, unsigned long long eb,
+                                               float iso) {
+  int a = (int)((ea >> (4 * k)) & 15), b = (int)((eb >> (4 * k)) & 15);
+  if ((d.swap >> k) & 1u) {
+    const int t = a; a = b; b = t;
+  }
+  const float4 pa = d.c[a], pb = d.c[b];
+  const float t = __fdiv_rn(__fsub_rn(iso, pa.w), __fsub_rn(pb.w, pa.w));
+  return make_float3(__fadd_rn(pa.x, __fmul_rn(t, __fsub_rn(pb.x, pa.x))),
+                     __fadd_rn(pa.y, __fmul_rn(t, __fsub_rn(pb.y, pa.y))),
+                     __fadd_rn(pa.z, __fmul_rn(t, __fsub_rn(pb.z, pa.z))));
+}
+
+__global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ BatchTable T,
+                                                    const float* __restrict__ isos,
+                                                    const long long* __restrict__ rel,
+                                                    const long long* __restrict__ off, float* __restrict__ tris,
+                                                    long long total_cap, const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
+  __shared__ unsigned tcnt[kMaxIso];        // rows of the tile taken so far, per iso-value
   __shared__ float iso_sh[kMaxIso];
-  __shared__ long long off_sh[kMaxIso + 1];
-  __shared__ long long tile_base;
-  __shared__ unsigned rows[256 * kRow];                     // each lane's dual: 8 vertex slots
-  __shared__ unsigned tlist[8][kTriStage];
-  __shared__ __align__(16) float tstage[8][kTriStage * 9];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned* myrow = rows + threadIdx.x * kRow;
+  __shared__ long long row0[kMaxIso];       // the tile's first row, per iso-value
+  __shared__ long long rowend[kMaxIso];     // end of the segment's rows that fit the buffer
+  __shared__ BatchVerts verts[256];         // each lane's dual
+  __shared__ unsigned tlist[8][kBatchStage];
+  __shared__ __align__(16) float tstage[8][kBatchStage * 9];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   unsigned* lst = tlist[w];
   float* wst = tstage[w];
+  BatchVerts& mine_v = verts[threadIdx.x];
   load_mc(sh, mc);
-  for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
-    iso_sh[k] = isos[k];
-    off_sh[k] = seg_off[k];
-  }
-  if (threadIdx.x == 0) off_sh[n_iso] = seg_off[n_iso];
-  __syncthreads();
-  for (;;) {
-    if (threadIdx.x == 0) tile_base = (long long)atomicAdd(&sc->tile, (unsigned long long)tile);
+  for (long long g = blockIdx.x; g < T.n_tiles; g += gridDim.x) {
+    const BatchJob& J = T.job[job_of_tile(T, g)];
+    const long long t = g - J.tile0;
+    for (int k = threadIdx.x; k < J.n_iso; k += blockDim.x) {
+      tcnt[k] = 0;
+      iso_sh[k] = __ldg(isos + J.q0 + k);
+      row0[k] = __ldg(off + J.q0 + k) + __ldg(rel + J.cbase + k * J.tiles + t);
+      rowend[k] = min(__ldg(off + J.q0 + k + 1), total_cap);
+    }
     __syncthreads();
-    const long long t0 = tile_base;
-    __syncthreads();
-    if (t0 >= nd) break;
-    const long long t1 = min(nd, t0 + tile);
-    for (long long base = t0 + (threadIdx.x & ~31); base < t1; base += blockDim.x) {
-      const long long d = base + lane;
-      unsigned v[8];
-      float sv[8];
-      float mn = 3.4e38f, mx = -3.4e38f;
-      const bool live = d < t1;
-      bool distinct = false;
-      if (live) {
-        distinct = load_dual(duals, d, v);
+    float lo_iso = 3.4e38f, hi_iso = -3.4e38f;   // range of the job's iso-values
+    for (int k = 0; k < J.n_iso; ++k) {
+      lo_iso = fminf(lo_iso, iso_sh[k]);
+      hi_iso = fmaxf(hi_iso, iso_sh[k]);
+    }
+    const long long d_hi = min(J.nd, (t + 1) * kBTile);
+    for (long long base = t * kBTile + 32 * w; base < d_hi; base += 32 * nw) {
+      BatchDual b;   // (its slots go to shared memory, the scalars stay in registers)
+      {
+        const long long d = base + lane;
+        b.live = d < d_hi;
+        b.distinct = false;
+        b.mn = 3.4e38f;
+        b.mx = -3.4e38f;
+        if (b.live) {
+          unsigned v[8];
+          b.distinct = load_dual(J.duals, d, v);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          sv[e] = __ldg(L.scal + v[e]);
-          mn = fminf(mn, sv[e]);
-          mx = fmaxf(mx, sv[e]);
-          myrow[e] = v[e];
+          for (int e = 0; e < 8; ++e) {
+            mine_v.v[e] = v[e];
+            b.s[e] = __ldg(J.scal + v[e]);
+            b.mn = fminf(b.mn, b.s[e]);
+            b.mx = fmaxf(b.mx, b.s[e]);
+          }
         }
       }
-      __syncwarp();
-      for (int k = 0; k < n_iso; ++k) {
-        const float iso = iso_sh[k];
-        unsigned keep = 0;
-        int cas = 0;
-        if (live && mx > iso && !(mn > iso)) {
+      if (b.live && b.mx > lo_iso && !(b.mn > hi_iso)) {   // some iso-value may cross it: its vertex data
+        // (z, y, x) order of the vertex cells' corners as one 64-bit key each:
+        // corners relative to vertex 0's, which they differ from by less
+        // than 2^16 per axis (every vertex cell holds a point within one
+        // cell width of the dual's owner)
+        unsigned long long key[8];
+        int4 c0 = make_int4(0, 0, 0, 0);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) cas |= (sv[e] > iso ? 1 : 0) << e;
-          keep = kept_of(distinct, sh.packed[cas], sh.count[cas], v, mc.edge_a, mc.edge_b);
+        for (int e = 0; e < 8; ++e) {
+          const int4 cr = slot_cell_rt(J.bricks, mine_v.v[e], J.logb);
+          if (e == 0) c0 = cr;
+          const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
+          mine_v.c[e] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
+                                    __fadd_rn(__int2float_rn(cr.z), h), b.s[e]);
+          key[e] = ((unsigned long long)(unsigned)(cr.z - c0.z + 65536) << 34) |
+                   ((unsigned long long)(unsigned)(cr.y - c0.y + 65536) << 17) | (unsigned)(cr.x - c0.x + 65536);
         }
+        // the hexahedron's 12 edges (a, b), a < b, in increasing order: the
+        // numbering the case table's edge ids use
+        constexpr int kEa[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6};
+        constexpr int kEb[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
+        unsigned sw = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) sw |= (key[kEb[k]] < key[kEa[k]] ? 1u : 0u) << k;
+        mine_v.swap = sw;
+      }
+      __syncwarp();
+      // the warp's scalar range: iso-values outside it cross none of its duals
+      const float lo = warp_min_f(b.mn), hi = warp_max_f(b.mx);
+      for (int k = 0; k < J.n_iso; ++k) {
+        const float iso = iso_sh[k];
+        if (!(hi > iso) || lo > iso) continue;   // uniform over the warp
+        int cas;
+        const unsigned keep = batch_keep(b, mine_v.v, iso, sh, mc.edge_a, mc.edge_b, cas);
         if (__ballot_sync(kFull, keep != 0) == 0) continue;
         const unsigned mine = __popc(keep);
-        const unsigned total = __reduce_add_sync(kFull, mine);
-        long long idx = warp_append(mine, &sc->n_tri[k]);
-        // rows of segment k that fit the buffer (all of them unless the
-        // caller's capacity was short)
-        const long long cap = max(0ll, min(off_sh[k + 1], total_cap) - off_sh[k]);
-        float* segk = tris + 9 * off_sh[k];
-        if (total <= (unsigned)kTriStage) {
-          const long long first = __shfl_sync(kFull, idx, 0);
-          unsigned pos = (unsigned)(idx - first);
-          const unsigned long long pk = sh.packed[cas];
-          for (int t = 0; t < 5; ++t)
-            if ((keep >> t) & 1u) lst[pos++] = (unsigned)lane | ((unsigned)(pk >> (12 * t)) & 0xFFFu) << 8;
+        unsigned incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        unsigned p0 = 0;
+        if (lane == 0) p0 = atomicAdd(&tcnt[k], total);
+        p0 = __shfl_sync(kFull, p0, 0);
+        const long long first = row0[k] + p0;            // the warp's first row
+        const long long end = rowend[k];
+        const unsigned long long pk = sh.packed[cas];
+        if (total <= (unsigned)kBatchStage) {
+          unsigned pos = incl - mine;
+          for (int tt = 0; tt < 5; ++tt)
+            if ((keep >> tt) & 1u) lst[pos++] = (unsigned)lane | ((unsigned)(pk >> (12 * tt)) & 0xFFFu) << 8;
           __syncwarp();
           for (unsigned q = lane; q < 3u * total; q += 32) {   // one vertex per lane
             const unsigned e = q / 3u, c = q - 3u * e;
             const unsigned ent = lst[e];
-            const unsigned* rv = rows + (w * 32 + (ent & 31u)) * kRow;
-            const int kk = (int)((ent >> (8 + 4 * c)) & 15u);
-            const int a = (int)((mc.edge_a >> (4 * kk)) & 15), b = (int)((mc.edge_b >> (4 * kk)) & 15);
-            const unsigned va = rv[a], vb = rv[b];
-            const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, va), __ldg(L.scal + va),
-                                         slot_cell<LOGB>(L.bricks, vb), __ldg(L.scal + vb), iso);
+            const float3 p = batch_vertex(verts[w * 32 + (ent & 31u)], (int)((ent >> (8 + 4 * c)) & 15u), mc.edge_a,
+                                          mc.edge_b, iso);
             wst[3 * q] = p.x;
             wst[3 * q + 1] = p.y;
             wst[3 * q + 2] = p.z;
           }
           __syncwarp();
-          const long long lim = min((long long)total, cap - first) * 9;   // capacity: exact prefix only
-          for (long long kk = lane; kk < lim; kk += 32) segk[9 * first + kk] = wst[kk];
-        } else if (keep) {   // more triangles than the stage holds: each lane writes its own
-          float* q0 = wst + lane * kRow;
+          const long long lim = min((long long)total, end - first) * 9;   // capacity: exact prefix only
+          for (long long kk = lane; kk < lim; kk += 32) tris[9 * first + kk] = wst[kk];
+        } else {   // more triangles than the stage holds: each lane writes its own
+          long long idx = first + incl - mine;
+          for (int tt = 0; tt < 5; ++tt) {
+            if (!((keep >> tt) & 1u)) continue;
+            if (idx < end) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) q0[e] = sv[e];
-          write_triangles<LOGB>(L.bricks, myrow, q0, iso, sh.packed[cas], keep, idx, cap, segk, mc.edge_a,
-                                mc.edge_b);
+              for (int c = 0; c < 3; ++c) {
+                const float3 p = batch_vertex(mine_v, (int)((pk >> (12 * tt + 4 * c)) & 15), mc.edge_a, mc.edge_b,
+                                              iso);
+                tris[9 * idx + 3 * c] = p.x;
+                tris[9 * idx + 3 * c + 1] = p.y;
+                tris[9 * idx + 3 * c + 2] = p.z;
+              }
+            }
+            ++idx;
+          }
         }
         __syncwarp();
       }
     }
+    __syncthreads();
   }
-}
-
-// Device-side segment offsets of a batch: exclusive prefix of the per-iso
-// counts of the count pass; resets the counters and the tile counter for the
-// emit pass. One thread; n_iso <= kMaxIso.
-__global__ void k_batch_offsets(Scratch* sc, int n_iso, long long* off) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  long long run = 0;
-  for (int k = 0; k < n_iso; ++k) {
-    off[k] = run;
-    run += (long long)sc->n_tri[k];
-    sc->n_tri[k] = 0;
-  }
-  off[n_iso] = run;
-  sc->tile = 0;
 }
 
 __global__ void __launch_bounds__(256) k_get_duals(const uint4* __restrict__ duals, long long nd,
@@ -1676,7 +1969,8 @@ cudaError_t launch_bin_coarse(int logb, const float* s, long long n, Locator loc
   if ((e = cudaFuncSetAttribute(k_bin_coarse<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
       (e = cudaFuncSetAttribute(k_bin_coarse<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCoarse)) ||
       (e = cudaFuncSetAttribute(k_bin_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFine)) ||
-      (e = cudaFuncSetAttribute(k_place_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)))
+      (e = cudaFuncSetAttribute(k_place_windows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)) ||
+      (e = cudaFuncSetAttribute(k_place_windows<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlace)))
     return e;
   if (n <= 0) return cudaSuccess;
   const long long tiles = (n + kCoarseTile - 1) / kCoarseTile;
@@ -1702,11 +1996,19 @@ cudaError_t launch_bin_fine(long long n_slots, void* staging, Scratch* sc, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_place_windows(long long n_slots, void* staging, unsigned long long* rec, cudaStream_t st) {
+cudaError_t launch_place_windows(int logb, long long n_slots, void* staging, unsigned long long* rec, unsigned* view,
+                                 float* scal, unsigned* elist, Scratch* sc, cudaStream_t st) {
   const BinLayout lay = bin_layout(n_slots);
   if (n_slots <= 0) return cudaSuccess;
   const Stages S = stages_of(lay, staging);
-  k_place_windows<<<(unsigned)lay.n_win, kPlaceThreads, kSmemPlace, st>>>(S.b, S.win_count, n_slots, rec);
+  AMR_DISPATCH(logb, (k_place_windows<LB><<<(unsigned)lay.n_win, kPlaceThreads, kSmemPlace, st>>>(
+                         S.b, S.win_count, n_slots, rec, view, scal, elist, sc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resolve_empty(int logb, Locator loc, const unsigned* elist, const Scratch* sc, unsigned* view,
+                                 int grid, cudaStream_t st) {
+  AMR_DISPATCH(logb, (k_resolve_empty<LB><<<grid, 256, 0, st>>>(loc, elist, sc, view)));
   return cudaGetLastError();
 }
 
@@ -1726,12 +2028,12 @@ cudaError_t launch_brick_neighbors(int logb, Locator loc, long long n_bricks, in
 }
 
 cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, const int* order, long long n_bricks,
-                              uint4* duals, long long cap, Scratch* sc, cudaStream_t st) {
+                              uint4* duals, long long cap, Scratch* sc, cudaStream_t st, int own_x0, int own_x1) {
   if (n_bricks <= 0) return cudaSuccess;
   const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
   McConst none{};
   AMR_DISPATCH(logb, (k_dual_cells<LB, false><<<grid, DualShape<LB>::kThreads, 0, st>>>(
-                         loc, nbr, order, n_bricks, duals, cap, sc, 0.f, nullptr, 0, none)));
+                         loc, nbr, order, n_bricks, duals, cap, sc, 0.f, nullptr, 0, own_x0, own_x1, none)));
   return cudaGetLastError();
 }
 
@@ -1741,7 +2043,7 @@ cudaError_t launch_dual_cells_iso(int logb, Locator loc, const int* nbr, const i
   if (n_bricks <= 0) return cudaSuccess;
   const int grid = (int)(n_bricks < (1ll << 30) ? n_bricks : (1ll << 30));
   AMR_DISPATCH(logb, (k_dual_cells<LB, true><<<grid, DualShape<LB>::kThreads, 0, st>>>(
-                         loc, nbr, order, n_bricks, duals, cap, sc, iso, tris, tri_cap, mc)));
+                         loc, nbr, order, n_bricks, duals, cap, sc, iso, tris, tri_cap, INT_MIN, INT_MAX, mc)));
   return cudaGetLastError();
 }
 
@@ -1749,6 +2051,8 @@ cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, f
                       long long cap, unsigned long long* counter, unsigned char* cases,
                       unsigned char* ntri, const McConst& mc, int grid, cudaStream_t st, long long* tags) {
   if (nd <= 0) return cudaSuccess;
+  // dynamic shared memory above the 48 KB default (an attribute of the
+  // current device's context, so set on every launch)
   if (cases || ntri) {
     AMR_DISPATCH(logb, (k_mc<LB, false, true><<<grid, 256, 0, st>>>(loc, duals, nd, iso, tris, cap, counter,
                                                                      cases, ntri, nullptr, mc)));
@@ -1761,8 +2065,6 @@ cudaError_t launch_mc(int logb, Locator loc, const uint4* duals, long long nd, f
                                                                          nullptr, nullptr, tags, mc);
     }));
   } else {
-    // dynamic shared memory above the 48 KB default (an attribute of the
-    // current device's context, so set on every launch)
     AMR_DISPATCH(logb, ({
       const cudaError_t e =
           cudaFuncSetAttribute(k_mc<LB, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMcSmemBytes);
@@ -1804,26 +2106,68 @@ cudaError_t launch_weld_index(const unsigned long long* tkeys, long long n_tri, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_mc_batch_count(int logb, Locator loc, const uint4* duals, long long nd,
-                                  const float* isos, int n_iso, Scratch* sc, const McConst& mc,
-                                  int grid, cudaStream_t st) {
-  if (nd <= 0) return cudaSuccess;
-  AMR_DISPATCH(logb, (k_mc_batch_count<LB><<<grid, 256, 0, st>>>(loc, duals, nd, isos, n_iso, sc, mc)));
+void batch_add_job(BatchTable& T, const uint4* duals, const float* scal, const int4* bricks, long long nd, int logb,
+                   int n_iso) {
+  BatchJob& J = T.job[T.n_jobs];
+  J.duals = duals;
+  J.scal = scal;
+  J.bricks = bricks;
+  J.nd = nd;
+  J.logb = logb;
+  J.tile0 = T.n_tiles;
+  J.tiles = (nd + kBTile - 1) / kBTile;
+  J.cbase = T.n_counters;
+  J.q0 = T.n_q;
+  J.n_iso = n_iso;
+  T.n_tiles += J.tiles;
+  T.n_counters += J.tiles * n_iso;
+  T.n_q += n_iso;
+  T.n_jobs += 1;
+}
+
+size_t batch_workspace_bytes(long long n_counters) { return (size_t)n_counters * 12 + 8 * (kMaxIso + 1); }
+
+namespace {
+struct BatchWs {
+  unsigned* counts;
+  long long* rel;
+  long long* totals;
+};
+BatchWs batch_ws(const BatchTable& T, void* ws) {
+  long long* rel = static_cast<long long*>(ws);
+  long long* totals = rel + T.n_counters;
+  unsigned* counts = reinterpret_cast<unsigned*>(totals + kMaxIso + 1);
+  return BatchWs{counts, rel, totals};
+}
+}  // namespace
+
+cudaError_t launch_batch_count(const BatchTable& T, const float* isos, void* ws, const McConst& mc, int grid,
+                               cudaStream_t st) {
+  if (T.n_tiles <= 0) return cudaSuccess;
+  const BatchWs W = batch_ws(T, ws);
+  k_batch_count<<<(unsigned)std::min<long long>(grid, T.n_tiles), 256, 0, st>>>(T, isos, W.counts, mc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long long nd,
-                                 const float* isos, int n_iso, float* tris, const long long* seg_off,
-                                 long long total_cap, Scratch* sc, const McConst& mc, int grid,
-                                 long long tile, cudaStream_t st) {
-  if (nd <= 0) return cudaSuccess;
-  AMR_DISPATCH(logb, (k_mc_batch_emit<LB><<<grid, 256, 0, st>>>(loc, duals, nd, isos, n_iso, tris, seg_off,
-                                                                 total_cap, sc, tile, mc)));
+cudaError_t launch_batch_scan(const BatchTable& T, void* ws, long long* off, cudaStream_t st) {
+  const BatchWs W = batch_ws(T, ws);
+  if (T.n_tiles > 0) {
+    k_batch_scan<<<(unsigned)T.n_q, kScanThreads, 0, st>>>(T, W.counts, W.rel, W.totals);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else {
+    const cudaError_t e = cudaMemsetAsync(W.totals, 0, sizeof(long long) * (kMaxIso + 1), st);
+    if (e != cudaSuccess) return e;
+  }
+  k_batch_bases<<<1, 32, 0, st>>>(T.n_q, W.totals, off);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_offsets(Scratch* sc, int n_iso, long long* off, cudaStream_t st) {
-  k_batch_offsets<<<1, 32, 0, st>>>(sc, n_iso, off);
+cudaError_t launch_batch_emit(const BatchTable& T, const float* isos, const void* ws, const long long* off,
+                              float* tris, long long cap, const McConst& mc, int grid, cudaStream_t st) {
+  if (T.n_tiles <= 0) return cudaSuccess;
+  const BatchWs W = batch_ws(T, const_cast<void*>(ws));
+  k_batch_emit<<<(unsigned)std::min<long long>(grid, T.n_tiles), 256, 0, st>>>(T, isos, W.rel, off, tris, cap, mc);
   return cudaGetLastError();
 }
 

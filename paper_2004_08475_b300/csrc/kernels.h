@@ -2,6 +2,7 @@
 // (api.cu). Nothing here is part of the public interface.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -20,7 +21,6 @@ enum ErrBits : uint32_t {
   ERR_DUPLICATE = 8u,
   ERR_OVERLAP = 16u,
   ERR_HASH_FULL = 32u,
-  ERR_TIMEOUT = 64u,
 };
 
 // Small device-resident counters, one allocation per context.
@@ -31,6 +31,7 @@ struct Scratch {
   unsigned long long n_tri[kMaxIso];    // per iso-value triangle counters
   unsigned long long n_occupied;        // occupied brick slots (= cells unless duplicates)
   unsigned long long n_vtx;             // welded vertices of an indexed face set
+  unsigned long long n_elist;           // bricks with empty slots (binned placement)
   unsigned int err;
   int lo[3];                            // bounding box: min lower corner
   int hi[3];                            // max (lower corner + width)
@@ -64,9 +65,9 @@ struct McConst {
 // brick_limit: once this many bricks exist the table counts as full
 // (ERR_HASH_FULL is raised and the remaining inserts stop early); bricks[]
 // must hold brick_limit entries. htab must be all ones before the launch.
-// codes (may be NULL; needs hcap << 3 log2_brick <= 2^32): per cell the
-// table entry of its brick << 3 log2_brick | its Morton index in the brick,
-// for launch_bin_coarse.
+// codes (may be NULL; needs hcap << 3 log2_brick <= 2^31): per cell its slot,
+// or (bit 31 set) the table entry of its brick << 3 log2_brick | its Morton
+// index in the brick, for launch_bin_coarse.
 cudaError_t launch_insert_bricks(int logb, const int* xyz, const unsigned char* lvl, const float* s,
                                  long long n, ulonglong2* htab,
                                  unsigned long long hmask, int4* bricks,
@@ -78,11 +79,11 @@ cudaError_t launch_scatter_cells(int logb, const int* xyz, const unsigned char* 
                                  long long n, Locator loc, unsigned long long* rec, Scratch* sc,
                                  int grid, int block, cudaStream_t st);
 
-// Binned cell placement, same result as launch_scatter_cells (three passes;
-// see kernels.cu). All three take the
-// same staging buffer of bin_layout(n_slots).bytes bytes; launch_bin_coarse
-// clears its counters first. Together they write every slot of rec (empty
-// slots as kEmptyRec).
+// Binned cell placement (three passes; see kernels.cu), same result as
+// launch_scatter_cells plus every slot's view (the slot itself where a cell
+// occupies it, else kReject until launch_resolve_empty) and scalar. All
+// three take the same staging buffer of bin_layout(n_slots).bytes bytes;
+// launch_bin_coarse clears its counters first.
 struct BinLayout {
   long long n_coarse = 0, n_win = 0, stage_a = 0, stage_b = 0;
   size_t bytes = 0;
@@ -92,7 +93,13 @@ BinLayout bin_layout(long long n_slots);
 cudaError_t launch_bin_coarse(int logb, const float* s, long long n, Locator loc, long long n_slots, void* staging,
                               Scratch* sc, int sm_count, const unsigned* codes, cudaStream_t st);
 cudaError_t launch_bin_fine(long long n_slots, void* staging, Scratch* sc, cudaStream_t st);
-cudaError_t launch_place_windows(long long n_slots, void* staging, unsigned long long* rec, cudaStream_t st);
+// Writes rec[], view[] and scal[] of every slot; elist[n_bricks] receives
+// the bricks with empty slots (counted by sc->n_elist, 0 before).
+cudaError_t launch_place_windows(int logb, long long n_slots, void* staging, unsigned long long* rec, unsigned* view,
+                                 float* scal, unsigned* elist, Scratch* sc, cudaStream_t st);
+// Resolves the empty slots of the listed bricks (view only).
+cudaError_t launch_resolve_empty(int logb, Locator loc, const unsigned* elist, const Scratch* sc, unsigned* view,
+                                 int grid, cudaStream_t st);
 
 // Writes view[] and scal[] of every slot from rec[].
 cudaError_t launch_resolve_views(int logb, Locator loc, unsigned* view, float* scal, long long n_slots,
@@ -104,9 +111,11 @@ cudaError_t launch_brick_neighbors(int logb, Locator loc, long long n_bricks, in
                                    cudaStream_t st);
 
 // order: NULL (bricks in index order) or a permutation of the bricks, the
-// order in which the CTAs visit them (see order.h).
+// order in which the CTAs visit them (see order.h). Only cells whose lower
+// corner's x lies in [own_x0, own_x1) emit their duals.
 cudaError_t launch_dual_cells(int logb, Locator loc, const int* nbr, const int* order, long long n_bricks,
-                              uint4* duals, long long cap, Scratch* sc, cudaStream_t st);
+                              uint4* duals, long long cap, Scratch* sc, cudaStream_t st, int own_x0 = INT_MIN,
+                              int own_x1 = INT_MAX);
 
 // Dual cells plus Marching Cubes at `iso` on each of them in the same pass;
 // triangles appended through sc->n_tri[0] (reset by the caller).
@@ -134,18 +143,47 @@ cudaError_t launch_weld_insert(int logb, Locator loc, const unsigned long long* 
 cudaError_t launch_weld_index(const unsigned long long* tkeys, long long n_tri, const ulonglong2* wtab,
                               unsigned long long wmask, int* tri, int grid, cudaStream_t st);
 
-cudaError_t launch_mc_batch_count(int logb, Locator loc, const uint4* duals, long long nd,
-                                  const float* isos, int n_iso, Scratch* sc, const McConst& mc,
-                                  int grid, cudaStream_t st);
+// Batched iso-values over one or several resident dual lists (see
+// kernels.cu): a job is one data set's dual list with its run of n_iso
+// iso-values; job j's iso-values are entries q0 .. q0 + n_iso - 1 of the
+// batch's iso array, and (job, value) q owns output segment q.
+constexpr int kBTile = 4096;   // duals per tile
+constexpr int kMaxJobs = 32;   // data sets in one batch
 
-// Segment k gets rows seg_off[k] .. seg_off[k+1]-1, clipped to total_cap.
-cudaError_t launch_mc_batch_emit(int logb, Locator loc, const uint4* duals, long long nd,
-                                 const float* isos, int n_iso, float* tris,
-                                 const long long* seg_off, long long total_cap, Scratch* sc,
-                                 const McConst& mc, int grid, long long tile, cudaStream_t st);
+struct BatchJob {
+  const uint4* duals;
+  const float* scal;
+  const int4* bricks;
+  long long nd;
+  long long tile0;   // first tile of this job in the batch's tile numbering
+  long long tiles;   // tiles of this job
+  long long cbase;   // first counter of this job: counters [n_iso][tiles]
+  int logb;
+  int q0;            // first segment (index into the batch's iso-values)
+  int n_iso;
+};
 
-// off[0..n_iso] = exclusive prefix of sc->n_tri; resets n_tri and tile.
-cudaError_t launch_batch_offsets(Scratch* sc, int n_iso, long long* off, cudaStream_t st);
+struct BatchTable {
+  int n_jobs = 0;
+  int n_q = 0;            // segments = iso-values of the batch (<= kMaxIso)
+  long long n_tiles = 0;
+  long long n_counters = 0;
+  BatchJob job[kMaxJobs];
+};
+
+// Appends a job (the caller checks n_jobs < kMaxJobs and n_q + n_iso <= kMaxIso).
+void batch_add_job(BatchTable& T, const uint4* duals, const float* scal, const int4* bricks, long long nd, int logb,
+                   int n_iso);
+// Device workspace of a batch with n_counters = T.n_counters.
+size_t batch_workspace_bytes(long long n_counters);
+// Per tile and iso-value the kept triangles (isos: the batch's device array).
+cudaError_t launch_batch_count(const BatchTable& T, const float* isos, void* ws, const McConst& mc, int grid,
+                               cudaStream_t st);
+// off[0..n_q]: each segment's first row and, last, the total (device).
+cudaError_t launch_batch_scan(const BatchTable& T, void* ws, long long* off, cudaStream_t st);
+// Segment q gets rows off[q] .. off[q+1]-1, clipped to cap.
+cudaError_t launch_batch_emit(const BatchTable& T, const float* isos, const void* ws, const long long* off,
+                              float* tris, long long cap, const McConst& mc, int grid, cudaStream_t st);
 
 cudaError_t launch_get_duals(const uint4* duals, long long nd, const unsigned long long* rec, int* out,
                              int grid, cudaStream_t st);

@@ -201,6 +201,7 @@ extern "C" int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level, con
     NA_TRY(rc_of(launch_mc(kLogB, L, duals, nd, iso, tris, cap, &sc->n_tri[0], nullptr, nullptr, mc, grid_d,
                            st)));
     NA_TRY(read_counters(sc, &h, st));
+    NA_TRY(err_bits(h.err));
     nt = (long long)h.n_tri[0];
   }
   *n_tris = nt;

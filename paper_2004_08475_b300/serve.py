@@ -5,12 +5,13 @@ locator and dual-cell list resident on the device (an `AmrContext`), so a new
 iso-value skips the dual-mesh pass; data sets are evicted least-recently-used
 when the device-memory budget is exceeded. Requests are batched continuously:
 ``slots`` worker threads, each with its own CUDA stream, take the oldest
-waiting request and every other waiting request for the same data set (up to
-64 iso-values in total) and serve them with one batched launch
-(`amr_iso_batch_async`, replayed from a captured CUDA graph once warm); one
-worker's dual-mesh pass ("prefill") overlaps another worker's iso work on the
-device. Latency = arrival -> triangles complete on the device and counts on
-the host.
+waiting request plus every other waiting request whose data set is resident
+and ready - whatever the data set, up to 64 iso-values and 32 data sets - and
+serve them with one batched launch over all their dual lists
+(`amr_iso_multi_async`, replayed from a captured CUDA graph when the same
+combination comes again); one worker's dual-mesh pass ("prefill") overlaps
+another worker's iso work on the device. Latency = arrival -> triangles
+complete on the device and counts on the host.
 
 The per-request plain extraction (FIFO; upload, locator, dual cells and one
 `amr_iso` per iso-value, no residency, no batching) is `serve_plain`.
@@ -29,6 +30,8 @@ import torch
 from . import amriso
 
 MAX_ISOS = 64
+MAX_JOBS = 32                   # data sets in one batched launch
+MAX_GRAPHS = 64                 # captured batch graphs kept per worker
 BYTES_PER_CELL_ESTIMATE = 110   # input copy + slots + dual list, before the real size is known
 
 
@@ -63,11 +66,9 @@ class _Dataset:
 class _Resident:
     def __init__(self, name, ctx, nbytes):
         self.name = name
-        self.ctx = ctx
+        self.ctx = ctx          # None while its dual-mesh pass runs
         self.bytes = nbytes
-        self.lock = threading.Lock()
-        self.users = 0
-        self.graphs = {}       # (worker, bucket) -> (graph, d_isos, out, d_offs)
+        self.users = 0          # batches (in any worker) that read it now
 
 
 class Server:
@@ -90,6 +91,8 @@ class Server:
         self.workers = []
         self.stats = collections.Counter()
         self._rid = 0
+        # captured batch graphs per worker: key (data sets, iso counts, buffers) -> graph
+        self.graphs: dict[int, "collections.OrderedDict"] = collections.defaultdict(collections.OrderedDict)
         # Graph capture must not overlap device allocation or release in other
         # threads (context creation, locator buffers, eviction, buffer growth);
         # kernel work and graph replays run outside this lock.
@@ -132,40 +135,65 @@ class Server:
         self.used = 0
 
     # -- scheduling ------------------------------------------------------------
+    def _ready(self, name: str) -> bool:
+        res = self.resident.get(name)
+        return res is not None and res.ctx is not None
+
+    def _pin(self, name: str) -> _Resident:
+        res = self.resident[name]
+        res.users += 1
+        self.resident.move_to_end(name)
+        return res
+
     def _take_batch(self):
-        """Oldest request plus every waiting request for the same data set whose
-        data set is not busy, up to MAX_ISOS iso-values. Caller holds cv."""
+        """The next batch, or None. Caller holds cv. Scans the queue oldest
+        first for a request that can start now:
+          - its data set is resident and ready: the batch takes it and every
+            later waiting request whose data set is resident and ready (any
+            data set), up to MAX_ISOS iso-values and MAX_JOBS data sets;
+          - its data set is not resident: the batch takes it and the later
+            requests for the same data set only, and a placeholder entry
+            (no context yet) marks the data set as being prepared;
+          - its data set is being prepared by another worker: skipped.
+        Every data set of the batch is pinned (users + 1) before cv is
+        released, so nothing the batch reads can be evicted, and a batch that
+        must wait for memory holds nothing else: no hold-and-wait. Returns
+        (requests, [(resident entry, needs its dual-mesh pass)])."""
         for i, head in enumerate(self.queue):
             res = self.resident.get(head.dataset)
-            if res is not None and res.users > 0:
-                continue   # another worker serves this data set; it will pick these up
+            if res is not None and res.ctx is None:
+                continue   # another worker prepares it; it will pick these up
+            fresh = res is None
             batch = [head]
+            names = [head.dataset]
             n = len(head.isos)
             for r in self.queue[i + 1:]:
-                if r.dataset == head.dataset and n + len(r.isos) <= MAX_ISOS:
+                if n + len(r.isos) > MAX_ISOS:
+                    continue
+                if r.dataset in names or (not fresh and len(names) < MAX_JOBS and self._ready(r.dataset)):
                     batch.append(r)
+                    if r.dataset not in names:
+                        names.append(r.dataset)
                     n += len(r.isos)
             for r in batch:
                 self.queue.remove(r)
-            return batch
+            if fresh:
+                res = _Resident(head.dataset, None, 0)
+                res.users = 1
+                self.resident[head.dataset] = res
+                return batch, [(res, True)]
+            return batch, [(self._pin(name), False) for name in names]
         return None
 
-    def _admit(self, name: str):
-        """Make room for `name` (LRU eviction of idle data sets) and mark it in
-        use. Caller holds cv; may wait until memory frees up. Returns the
-        resident entry, whether it still needs its dual-mesh pass, and the
-        evicted contexts (to be closed by the caller outside cv)."""
+    def _reserve(self, res: _Resident):
+        """Device memory for a placeholder entry's dual-mesh pass: evict idle
+        data sets least-recently-used first until the estimate fits (or
+        nothing else is resident). Caller holds cv; waits while other
+        batches hold what would have to go. Returns the evicted contexts (the
+        caller closes them outside cv)."""
+        need = self.datasets[res.name].xyz.shape[0] * BYTES_PER_CELL_ESTIMATE
         evicted = []
         while True:
-            res = self.resident.get(name)
-            if res is not None:
-                if res.users > 0:          # another worker holds it (a context is
-                    self.cv.wait(0.005)    # single-threaded); its prefill may be running
-                    continue
-                res.users += 1
-                self.resident.move_to_end(name)
-                return res, False, evicted
-            need = self.datasets[name].xyz.shape[0] * BYTES_PER_CELL_ESTIMATE
             while self.used + need > self.budget:
                 victim = next((r for r in self.resident.values() if r.users == 0), None)
                 if victim is None:
@@ -175,17 +203,24 @@ class Server:
                     evicted.append(victim.ctx)
                 self.used -= victim.bytes
                 self.stats["evictions"] += 1
-            if self.used + need <= self.budget or not self.resident:
-                res = _Resident(name, None, need)
-                res.users = 1
-                self.resident[name] = res
+                self._drop_graphs(victim.name)
+            if self.used + need <= self.budget or all(r is res for r in self.resident.values()):
                 self.used += need
-                return res, True, evicted
+                res.bytes = need
+                return evicted
             self.cv.wait(0.01)
 
-    def _release(self, res: _Resident):
+    def _drop_graphs(self, name: str):
+        """Forget every captured graph that reads data set `name` (its device
+        buffers are about to go). Caller holds cv."""
+        for g in self.graphs.values():
+            for key in [k for k in g if name in k[0]]:
+                del g[key]
+
+    def _release(self, residents):
         with self.cv:
-            res.users -= 1
+            for res in residents:
+                res.users -= 1
             self.cv.notify_all()
 
     # -- worker ----------------------------------------------------------------
@@ -193,11 +228,12 @@ class Server:
         torch.cuda.set_device(self.device)
         with self.cuda_lock:
             stream = torch.cuda.Stream(self.device)
-            out = torch.empty((self.out_capacity, 3, 3), dtype=torch.float32, device=self.device)
-            d_isos = torch.empty(MAX_ISOS, dtype=torch.float32, device=self.device)
-            d_offs = torch.zeros(MAX_ISOS + 1, dtype=torch.int64, device=self.device)
-        h_offs = torch.zeros(MAX_ISOS + 1, dtype=torch.int64).pin_memory()
-        h_isos = torch.empty(MAX_ISOS, dtype=torch.float32).pin_memory()
+            bufs = {"out": torch.empty((self.out_capacity, 3, 3), dtype=torch.float32, device=self.device),
+                    "ws": torch.empty(1 << 20, dtype=torch.uint8, device=self.device),
+                    "d_isos": torch.empty(MAX_ISOS, dtype=torch.float32, device=self.device),
+                    "d_offs": torch.zeros(MAX_ISOS + 1, dtype=torch.int64, device=self.device)}
+        bufs["h_offs"] = torch.zeros(MAX_ISOS + 1, dtype=torch.int64).pin_memory()
+        bufs["h_isos"] = torch.empty(MAX_ISOS, dtype=torch.float32).pin_memory()
         while True:
             with self.cv:
                 batch = None
@@ -208,7 +244,11 @@ class Server:
                     self.cv.wait(0.005)
                 if self.stop_flag and not batch:
                     return
-                res, fresh, evicted = self._admit(batch[0].dataset)
+                batch, admitted = batch
+                evicted = []
+                for res, fresh in admitted:
+                    if fresh:
+                        evicted += self._reserve(res)
             if evicted:
                 with self.cuda_lock:
                     for ctx in evicted:
@@ -218,16 +258,17 @@ class Server:
                 r.t_start = t0
             try:
                 with torch.cuda.stream(stream):
-                    if fresh:
-                        self._prefill(res, stream)
-                    out = self._serve(w, res, batch, stream, out, d_isos, d_offs, h_offs, h_isos)
+                    for res, fresh in admitted:
+                        if fresh:
+                            self._prefill(res, stream)
+                    self._serve(w, [res for res, _ in admitted], batch, stream, bufs)
             except Exception:  # report per request, keep serving
                 err = traceback.format_exc()
                 for r in batch:
                     r.error = err
-                if res.ctx is None:                 # failed dual-mesh pass: forget the entry
-                    with self.cv:
-                        if self.resident.get(res.name) is res:
+                with self.cv:
+                    for res, fresh in admitted:
+                        if fresh and res.ctx is None and self.resident.get(res.name) is res:   # failed prefill
                             self.resident.pop(res.name)
                             self.used -= res.bytes
             t1 = time.perf_counter()
@@ -237,7 +278,9 @@ class Server:
                 r.done.set()
             self.stats["batches"] += 1
             self.stats["requests"] += len(batch)
-            self._release(res)
+            if len(admitted) > 1:
+                self.stats["multi_dataset_batches"] += 1
+            self._release([res for res, _ in admitted])
 
     def _prefill(self, res: _Resident, stream):
         ds = self.datasets[res.name]
@@ -258,57 +301,91 @@ class Server:
             res.ctx = ctx
         self.stats["prefills"] += 1
 
-    def _serve(self, w, res, batch, stream, out, d_isos, d_offs, h_offs, h_isos):
-        ctx = res.ctx
-        ctx.set_stream(stream)
-        isos = [v for r in batch for v in r.isos]
-        k = len(isos)
-        bucket = 1
-        while bucket < k:
-            bucket *= 2
-        padded = isos + [float("inf")] * (bucket - k)   # +inf: no corner is above it, no triangles
-        h_isos[:bucket] = torch.tensor(padded, dtype=torch.float32)
-        d_isos[:bucket].copy_(h_isos[:bucket], non_blocking=True)
-        # the graph bakes in the buffer's address and capacity: both are in the key
-        key = (w, bucket, out.data_ptr(), int(out.shape[0]))
-        g = res.graphs.get(key) if self.use_graphs else None
+    def _serve(self, w, residents, batch, stream, bufs):
+        """One batched launch over the batch's data sets: job j = residents[j]
+        at the iso-values of its requests (in batch order), each job's count
+        padded with +inf up to a power of two when the padded total fits
+        (+inf: no corner lies above it, so no triangles), so that recurring
+        combinations replay one captured graph."""
+        per = {res.name: [] for res in residents}
+        for r in batch:
+            per[r.dataset].extend(r.isos)
+        counts = [len(per[res.name]) for res in residents]
+        padded = [1 << (k - 1).bit_length() for k in counts]
+        if sum(padded) > MAX_ISOS:
+            padded = counts
+        isos = []
+        for res, k, p in zip(residents, counts, padded):
+            isos += per[res.name] + [float("inf")] * (p - k)
+        nq = len(isos)
+        ctxs = [res.ctx for res in residents]
+        bufs["h_isos"][:nq] = torch.tensor(isos, dtype=torch.float32)
+        bufs["d_isos"][:nq].copy_(bufs["h_isos"][:nq], non_blocking=True)
+        need_ws = amriso.iso_multi_workspace(ctxs, padded)
+        if need_ws > bufs["ws"].numel():
+            with self.cuda_lock:
+                bufs["ws"] = torch.empty(int(need_ws * 1.5), dtype=torch.uint8, device=self.device)
+            with self.cv:
+                self.graphs[w].clear()
+        out, ws = bufs["out"], bufs["ws"]
+        d_isos, d_offs = bufs["d_isos"][:nq], bufs["d_offs"][:nq + 1]
+        # a graph bakes in the data sets' buffers, the iso counts and the
+        # worker's buffers (address and capacity): all are in the key
+        key = (tuple(res.name for res in residents), tuple(padded), tuple(id(c) for c in ctxs),
+               out.data_ptr(), int(out.shape[0]), ws.data_ptr())
+        graphs = self.graphs[w]
+        with self.cv:   # other workers drop graphs of evicted data sets under cv
+            g = graphs.get(key) if self.use_graphs else None
+            if g is not None:
+                graphs.move_to_end(key)
+
+        def launch():
+            amriso.iso_multi_async(ctxs, padded, d_isos, out, d_offs, ws, stream)
+
         if g is not None:
             g.replay()
             self.stats["graph_replays"] += 1
         else:
-            ctx.iso_batch_async(d_isos[:bucket], out, d_offs[:bucket + 1])
+            launch()
             if self.use_graphs:
-                res.graphs[key] = self._capture(ctx, stream, d_isos[:bucket], out, d_offs[:bucket + 1])
-        h_offs[:bucket + 1].copy_(d_offs[:bucket + 1], non_blocking=True)
+                g = self._capture(launch, stream)
+                with self.cv:
+                    graphs[key] = g
+                    while len(graphs) > MAX_GRAPHS:
+                        graphs.popitem(last=False)
+        bufs["h_offs"][:nq + 1].copy_(d_offs, non_blocking=True)
         stream.synchronize()
-        offs = h_offs[:bucket + 1].tolist()
-        if offs[bucket] > out.shape[0]:     # buffer too small: grow, drop stale graphs, rerun
+        offs = bufs["h_offs"][:nq + 1].tolist()
+        if offs[nq] > out.shape[0]:     # buffer too small: grow, drop this worker's graphs, rerun
             with self.cuda_lock:
-                out = torch.empty((int(offs[bucket] * 1.25) + 1, 3, 3), dtype=torch.float32,
-                                  device=self.device)
-            with self.cv:   # this worker's graphs on every resident data set point at the old buffer
-                for other in self.resident.values():
-                    for gk in [gk for gk in other.graphs if gk[0] == w]:
-                        del other.graphs[gk]
-            ctx.iso_batch_async(d_isos[:bucket], out, d_offs[:bucket + 1])
-            h_offs[:bucket + 1].copy_(d_offs[:bucket + 1], non_blocking=True)
+                out = bufs["out"] = torch.empty((int(offs[nq] * 1.25) + 1, 3, 3), dtype=torch.float32,
+                                                device=self.device)
+            with self.cv:
+                self.graphs[w].clear()
+            amriso.iso_multi_async(ctxs, padded, d_isos, out, d_offs, ws, stream)
+            bufs["h_offs"][:nq + 1].copy_(d_offs, non_blocking=True)
             stream.synchronize()
-            offs = h_offs[:bucket + 1].tolist()
-        j = 0
+            offs = bufs["h_offs"][:nq + 1].tolist()
+        first = {}
+        q = 0
+        for res, p in zip(residents, padded):
+            first[res.name] = q
+            q += p
+        taken = collections.Counter()
         for r in batch:
-            r.counts = [offs[j + q + 1] - offs[j + q] for q in range(len(r.isos))]
+            j = first[r.dataset] + taken[r.dataset]
+            taken[r.dataset] += len(r.isos)
+            r.counts = [offs[j + i + 1] - offs[j + i] for i in range(len(r.isos))]
             if self.keep_results:
-                r.tris = [out[offs[j + q]:offs[j + q + 1]].cpu() for q in range(len(r.isos))]
-            j += len(r.isos)
-        return out
+                r.tris = [out[offs[j + i]:offs[j + i + 1]].cpu() for i in range(len(r.isos))]
 
-    def _capture(self, ctx, stream, d_isos, out, d_offs):
-        """CUDA graph of the batched step (count, device offsets, emit)."""
+    def _capture(self, launch, stream):
+        """CUDA graph of the batched step (counts, prefix sums, emission)."""
         stream.synchronize()
         g = torch.cuda.CUDAGraph()
         with self.cuda_lock:
             with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
-                ctx.iso_batch_async(d_isos, out, d_offs)
+                launch()
         return g
 
 

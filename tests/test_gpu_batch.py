@@ -111,3 +111,41 @@ def test_batch_async_short_capacity():
         assert sum(got.values()) == hi - lo
         assert all(want[r] >= c for r, c in got.items()), f"segment {k}: a row that is not the oracle's"
     ctx.close()
+
+
+def test_multi_dataset_batch_matches_oracle():
+    """One batch over three data sets of different sizes, depths and brick
+    sizes (amr_iso_multi_async): every (data set, iso-value) segment holds
+    exactly the oracle's triangles."""
+    from paper_2004_08475_b300 import amriso
+    sets = [(_reduced_wing(), 3, 5), (synth.random_octree(31, levels=4, roots=5, p_split=0.45, p_hole=0.06,
+                                                          field="random"), 2, 3),
+            (synth.sphere_tiny(), 3, 2)]
+    ctxs, isos, n_isos, refs = [], [], [], []
+    for (xyz, lv, s, iso0, info), logb, k in sets:
+        ctx = amriso.AmrContext()
+        ctx.upload(xyz.cuda(), lv.cuda(), s.cuda())
+        ctx.build_locator(log2_brick=logb)
+        ctx.dual_cells()
+        vals = [float(np.float32(iso0 * (0.8 + 0.15 * q))) for q in range(k)]
+        ctxs.append(ctx)
+        isos += vals
+        n_isos.append(k)
+        m = oracle.OracleMesh(xyz.numpy(), lv.numpy())
+        d = m.duals()
+        refs += [m.iso(s.numpy(), d, np.float32(v), want_keys=False)["tris"] for v in vals]
+    total = sum(r.shape[0] for r in refs)
+    ws = torch.empty(amriso.iso_multi_workspace(ctxs, n_isos), dtype=torch.uint8, device="cuda")
+    out = torch.empty((total + 16, 3, 3), dtype=torch.float32, device="cuda")
+    d_iso = torch.tensor(isos, dtype=torch.float32, device="cuda")
+    d_off = torch.zeros(len(isos) + 1, dtype=torch.int64, device="cuda")
+    amriso.iso_multi_async(ctxs, n_isos, d_iso, out, d_off, ws)
+    torch.cuda.synchronize()
+    offs = d_off.cpu().tolist()
+    assert offs[-1] == total > 0
+    for q, ref in enumerate(refs):
+        seg = out[offs[q]:offs[q + 1]].cpu().numpy()
+        assert seg.shape[0] == ref.shape[0], q
+        assert (canonical(seg) == canonical(ref)).all(), q
+    for c in ctxs:
+        c.close()

@@ -29,6 +29,7 @@ def _server(budget):
     srv.used = 0
     srv.stats = __import__("collections").Counter()
     srv._rid = 0
+    srv.graphs = __import__("collections").defaultdict(__import__("collections").OrderedDict)
     return srv, _Resident
 
 
@@ -41,20 +42,43 @@ def test_batch_coalesces_same_dataset_up_to_64_isos():
     srv, _ = _server(1 << 30)
     srv.queue = [_req(1, "a", 10), _req(2, "b", 3), _req(3, "a", 40), _req(4, "a", 20), _req(5, "a", 5)]
     with srv.cv:
-        batch = srv._take_batch()
+        batch, entries = srv._take_batch()
     assert [r.rid for r in batch] == [1, 3, 5]          # 10 + 40 + 5 <= 64; 20 would exceed
     assert [r.rid for r in srv.queue] == [2, 4]
+    (res, fresh), = entries                             # a needs its dual-mesh pass: a placeholder
+    assert fresh and res.ctx is None and srv.resident["a"] is res and res.users == 1
 
 
-def test_batch_skips_dataset_in_use():
+def test_batch_skips_dataset_being_prepared():
     srv, Res = _server(1 << 30)
-    busy = Res("a", _FakeCtx(), 10)
+    busy = Res("a", None, 10)   # another worker runs its dual-mesh pass
     busy.users = 1
     srv.resident["a"] = busy
     srv.queue = [_req(1, "a", 1), _req(2, "b", 1)]
     with srv.cv:
-        batch = srv._take_batch()
+        batch, entries = srv._take_batch()
     assert [r.rid for r in batch] == [2]
+
+
+def test_batch_joins_ready_datasets():
+    """Requests for other data sets join a batch whose head is ready when
+    those are resident and ready (even while another batch reads them), not
+    when they still need their dual-mesh pass; a batch whose head needs its
+    dual-mesh pass takes nothing else. Every data set taken is pinned."""
+    srv, Res = _server(1 << 30)
+    for name in ("a", "c"):
+        srv.resident[name] = Res(name, _FakeCtx(), 10)
+    srv.resident["c"].users = 1
+    srv.queue = [_req(1, "a", 3), _req(2, "b", 2), _req(3, "d", 1), _req(4, "c", 62), _req(5, "c", 4)]
+    with srv.cv:
+        batch, entries = srv._take_batch()
+    assert [r.rid for r in batch] == [1, 5]             # b, d not resident; c's 62 would pass 64 values
+    assert [(e.name, fresh) for e, fresh in entries] == [("a", False), ("c", False)]
+    assert srv.resident["a"].users == 1 and srv.resident["c"].users == 2
+    with srv.cv:
+        batch, entries = srv._take_batch()
+    assert [r.rid for r in batch] == [2] and entries[0][1]   # b alone, as a placeholder
+    assert [r.rid for r in srv.queue] == [3, 4]
 
 
 def test_lru_eviction_under_budget():
@@ -68,20 +92,25 @@ def test_lru_eviction_under_budget():
     old = serve.BYTES_PER_CELL_ESTIMATE
     serve.BYTES_PER_CELL_ESTIMATE = 100          # 400 bytes per data set
     try:
-        for name in ("a", "b"):
+        for rid, name in enumerate(("a", "b")):
+            srv.queue = [_req(rid, name, 1)]
             with srv.cv:
-                res, fresh, ev = srv._admit(name)
-            assert fresh and not ev
+                _, entries = srv._take_batch()
+                (res, fresh), = entries
+                assert fresh and not srv._reserve(res)
             res.ctx = _FakeCtx()
-            res.users = 0
-        with srv.cv:                              # touch a: b becomes least recent
-            res, fresh, ev = srv._admit("a")
-        assert not fresh
-        res.users = 0
-        victim_ctx = srv.resident["b"].ctx
+            srv._release([res])
+        srv.queue = [_req(3, "a", 1)]            # touch a: b becomes least recent
         with srv.cv:
-            res, fresh, ev = srv._admit("c")      # 1200 > 1000: evict b
-        assert fresh and "b" not in srv.resident and ev == [victim_ctx]
+            _, entries = srv._take_batch()
+        assert not entries[0][1]
+        srv._release([entries[0][0]])
+        victim_ctx = srv.resident["b"].ctx
+        srv.queue = [_req(4, "c", 1)]
+        with srv.cv:
+            _, entries = srv._take_batch()
+            ev = srv._reserve(entries[0][0])      # 1200 > 1000: evict b
+        assert "b" not in srv.resident and ev == [victim_ctx]
         assert srv.stats["evictions"] == 1 and srv.used == 800
     finally:
         serve.BYTES_PER_CELL_ESTIMATE = old
