@@ -444,9 +444,12 @@ class ServeBench:
         return [self.serve.Request(r.rid, r.dataset, list(r.isos), r.t_arrival) for r in reqs]
 
     def run_server(self, reqs, budget):
+        """The server, its data sets preloaded (most popular first) up to the
+        budget before the stream starts; requests beyond it evict LRU."""
         srv = self.serve.Server(budget_bytes=budget, slots=self.slots)
         for name, (x, l, v) in self.host.items():
             srv.datasets[name] = self.serve._Dataset(name, x, l, v, {})
+        srv.preload([self.names[i] for i in np.argsort(-self.prob)])
         srv.start()
         t_base = time.perf_counter() + 0.05
         for r in reqs:

@@ -115,6 +115,25 @@ __device__ __forceinline__ int4 slot_cell(const int4* __restrict__ bricks, unsig
 
 __device__ __forceinline__ unsigned warp_or(unsigned v) { return __reduce_or_sync(kFull, v); }
 
+// Morton index inside a brick -> cell offsets x | y << 4 | z << 8, as a
+// shared-memory table (filled by fill_cell_table before a barrier): one
+// load instead of the bit compaction per axis in the vertex loops.
+template <int LOGB>
+__device__ __forceinline__ void fill_cell_table(unsigned short* tab) {
+  for (int m = threadIdx.x; m < (1 << (3 * LOGB)); m += blockDim.x)
+    tab[m] = (unsigned short)(compact<LOGB>(m) | (compact<LOGB>(m >> 1) << 4) | (compact<LOGB>(m >> 2) << 8));
+}
+
+// slot_cell through the table.
+template <int LOGB>
+__device__ __forceinline__ int4 slot_cell_tab(const int4* __restrict__ bricks, const unsigned short* tab,
+                                              unsigned slot) {
+  const int4 b = __ldg(bricks + (slot >> (3 * LOGB)));
+  const unsigned t = tab[slot & ((1u << (3 * LOGB)) - 1u)];
+  return make_int4(b.x + ((int)(t & 15u) << b.w), b.y + ((int)((t >> 4) & 15u) << b.w),
+                   b.z + ((int)(t >> 8) << b.w), b.w);
+}
+
 // ---------------------------------------------------------------------------
 // Locator build (Sec. 3.2)
 // ---------------------------------------------------------------------------
@@ -1619,16 +1638,18 @@ __global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ Bat
     }
     __syncthreads();
     const long long d_hi = min(J.nd, (t + 1) * kBTile);
-    for (long long base = t * kBTile + 32 * w; base < d_hi; base += 32 * nw) {
-      BatchDual b;
-      batch_load(J, base + lane, d_hi, b);
+    for (long long base = t * kBTile + 64 * w; base < d_hi; base += 64 * nw) {   // two duals per lane
+      BatchDual b0, b1;
+      batch_load(J, base + lane, d_hi, b0);
+      batch_load(J, base + 32 + lane, d_hi, b1);
       // the warp's scalar range: iso-values outside it cross none of its duals
-      const float lo = warp_min_f(b.mn), hi = warp_max_f(b.mx);
+      const float lo = warp_min_f(fminf(b0.mn, b1.mn)), hi = warp_max_f(fmaxf(b0.mx, b1.mx));
       for (int k = 0; k < J.n_iso; ++k) {
         if (!(hi > iso_sh[k]) || lo > iso_sh[k]) continue;   // uniform over the warp
         int cas;
-        const unsigned keep = batch_keep(b, b.v, iso_sh[k], sh, mc.edge_a, mc.edge_b, cas);
-        const unsigned c = __reduce_add_sync(kFull, (unsigned)__popc(keep));
+        unsigned c = __popc(batch_keep(b0, b0.v, iso_sh[k], sh, mc.edge_a, mc.edge_b, cas));
+        c += __popc(batch_keep(b1, b1.v, iso_sh[k], sh, mc.edge_a, mc.edge_b, cas));
+        c = __reduce_add_sync(kFull, c);
         if (lane == 0 && c) atomicAdd(&cnt[k], c);
       }
     }
@@ -1718,7 +1739,9 @@ struct BatchVerts {
   unsigned swap;      // bit k: edge k's vertex b comes first
   unsigned pad[3];
 };
-constexpr int kBatchStage = 64;   // triangles a warp stages per step and iso-value
+// Triangles a warp lists per step over all its iso-values before computing
+// their vertices (one iso-value adds at most 32 duals x 5 triangles).
+constexpr int kBatchList = 256;
 
 __device__ __forceinline__ float3 batch_vertex(const BatchVerts& d, int k, unsigned long long ea, unsigned long long eb,
                                                float iso) {
@@ -1733,6 +1756,35 @@ __device__ __forceinline__ float3 batch_vertex(const BatchVerts& d, int k, unsig
                      __fadd_rn(pa.z, __fmul_rn(t, __fsub_rn(pb.z, pa.z))));
 }
 
+// List entry of k_batch_emit: the triangle's row inside its tile's run of
+// its segment (bits 0-31), the lane whose dual it belongs to (32-36), the
+// iso-value (37-42) and its three edge ids (43-54).
+__device__ __forceinline__ unsigned long long batch_entry(unsigned row, unsigned lane, unsigned k, unsigned edges) {
+  return (unsigned long long)row | ((unsigned long long)lane << 32) | ((unsigned long long)k << 37) |
+         ((unsigned long long)edges << 43);
+}
+
+// The warp's listed triangles, one vertex per lane in turn: interpolated
+// from the listing lane's vertex data and written straight to its row (a
+// run of consecutive rows per segment, so consecutive lanes write
+// consecutive 12-byte vertices).
+__device__ __forceinline__ void batch_flush(const unsigned long long* lst, unsigned len, const BatchVerts* wverts,
+                                            const float* iso_sh, const long long* row0, const long long* rowend,
+                                            float* __restrict__ tris, unsigned long long ea, unsigned long long eb) {
+  for (unsigned q = threadIdx.x & 31; q < 3u * len; q += 32) {
+    const unsigned e = q / 3u, c = q - 3u * e;
+    const unsigned long long ent = lst[e];
+    const unsigned k = (unsigned)(ent >> 37) & 63u;
+    const long long row = row0[k] + (long long)(unsigned)ent;
+    if (row >= rowend[k]) continue;   // capacity: exact prefix only
+    const float3 p = batch_vertex(wverts[(ent >> 32) & 31u], (int)((ent >> (43 + 4 * c)) & 15u), ea, eb, iso_sh[k]);
+    float* out = tris + 9 * row + 3 * c;
+    out[0] = p.x;
+    out[1] = p.y;
+    out[2] = p.z;
+  }
+}
+
 __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ BatchTable T,
                                                     const float* __restrict__ isos,
                                                     const long long* __restrict__ rel,
@@ -1744,11 +1796,9 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
   __shared__ long long row0[kMaxIso];       // the tile's first row, per iso-value
   __shared__ long long rowend[kMaxIso];     // end of the segment's rows that fit the buffer
   __shared__ BatchVerts verts[256];         // each lane's dual
-  __shared__ unsigned tlist[8][kBatchStage];
-  __shared__ __align__(16) float tstage[8][kBatchStage * 9];
+  __shared__ unsigned long long tlist[8][kBatchList];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned* lst = tlist[w];
-  float* wst = tstage[w];
+  unsigned long long* lst = tlist[w];
   BatchVerts& mine_v = verts[threadIdx.x];
   load_mc(sh, mc);
   for (long long g = blockIdx.x; g < T.n_tiles; g += gridDim.x) {
@@ -1816,12 +1866,12 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
       __syncwarp();
       // the warp's scalar range: iso-values outside it cross none of its duals
       const float lo = warp_min_f(b.mn), hi = warp_max_f(b.mx);
+      unsigned len = 0;   // entries in the warp's list
       for (int k = 0; k < J.n_iso; ++k) {
         const float iso = iso_sh[k];
         if (!(hi > iso) || lo > iso) continue;   // uniform over the warp
         int cas;
         const unsigned keep = batch_keep(b, mine_v.v, iso, sh, mc.edge_a, mc.edge_b, cas);
-        if (__ballot_sync(kFull, keep != 0) == 0) continue;
         const unsigned mine = __popc(keep);
         unsigned incl = mine;
 #pragma unroll
@@ -1830,48 +1880,26 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
           if (lane >= o) incl += y;
         }
         const unsigned total = __shfl_sync(kFull, incl, 31);
-        unsigned p0 = 0;
-        if (lane == 0) p0 = atomicAdd(&tcnt[k], total);
-        p0 = __shfl_sync(kFull, p0, 0);
-        const long long first = row0[k] + p0;            // the warp's first row
-        const long long end = rowend[k];
-        const unsigned long long pk = sh.packed[cas];
-        if (total <= (unsigned)kBatchStage) {
-          unsigned pos = incl - mine;
-          for (int tt = 0; tt < 5; ++tt)
-            if ((keep >> tt) & 1u) lst[pos++] = (unsigned)lane | ((unsigned)(pk >> (12 * tt)) & 0xFFFu) << 8;
+        if (total == 0) continue;
+        if (len + total > (unsigned)kBatchList) {   // list full: its vertices first
           __syncwarp();
-          for (unsigned q = lane; q < 3u * total; q += 32) {   // one vertex per lane
-            const unsigned e = q / 3u, c = q - 3u * e;
-            const unsigned ent = lst[e];
-            const float3 p = batch_vertex(verts[w * 32 + (ent & 31u)], (int)((ent >> (8 + 4 * c)) & 15u), mc.edge_a,
-                                          mc.edge_b, iso);
-            wst[3 * q] = p.x;
-            wst[3 * q + 1] = p.y;
-            wst[3 * q + 2] = p.z;
-          }
+          batch_flush(lst, len, verts + w * 32, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
           __syncwarp();
-          const long long lim = min((long long)total, end - first) * 9;   // capacity: exact prefix only
-          for (long long kk = lane; kk < lim; kk += 32) tris[9 * first + kk] = wst[kk];
-        } else {   // more triangles than the stage holds: each lane writes its own
-          long long idx = first + incl - mine;
-          for (int tt = 0; tt < 5; ++tt) {
-            if (!((keep >> tt) & 1u)) continue;
-            if (idx < end) {
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const float3 p = batch_vertex(mine_v, (int)((pk >> (12 * tt + 4 * c)) & 15), mc.edge_a, mc.edge_b,
-                                              iso);
-                tris[9 * idx + 3 * c] = p.x;
-                tris[9 * idx + 3 * c + 1] = p.y;
-                tris[9 * idx + 3 * c + 2] = p.z;
-              }
-            }
-            ++idx;
-          }
+          len = 0;
         }
-        __syncwarp();
+        unsigned p0 = 0;
+        if (lane == 0) p0 = atomicAdd(&tcnt[k], total);   // rows inside the tile's run of segment k
+        p0 = __shfl_sync(kFull, p0, 0);
+        unsigned pos = len + incl - mine, row = p0 + incl - mine;
+        const unsigned long long pk = sh.packed[cas];
+        for (int tt = 0; tt < 5; ++tt)
+          if ((keep >> tt) & 1u)
+            lst[pos++] = batch_entry(row++, (unsigned)lane, (unsigned)k, (unsigned)(pk >> (12 * tt)) & 0xFFFu);
+        len += total;
       }
+      __syncwarp();
+      batch_flush(lst, len, verts + w * 32, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
+      __syncwarp();
     }
     __syncthreads();
   }

@@ -115,6 +115,28 @@ class Server:
             self.cv.notify_all()
         return r
 
+    def preload(self, names=None):
+        """Run the dual-mesh pass of data sets before serving starts (in the
+        given order, all registered ones by default) while their estimated
+        size fits the budget: a server starts with its data sets resident.
+        Call before start()."""
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(self.device)
+        for name in (names if names is not None else list(self.datasets)):
+            with self.cv:
+                if name in self.resident:
+                    continue
+                if self.used + self.datasets[name].xyz.shape[0] * BYTES_PER_CELL_ESTIMATE > self.budget:
+                    break
+                res = _Resident(name, None, 0)
+                res.users = 1
+                self.resident[name] = res
+                self._reserve(res)
+            with torch.cuda.stream(stream):
+                self._prefill(res, stream)
+            self._release([res])
+        torch.cuda.synchronize()
+
     def start(self):
         for w in range(self.slots):
             th = threading.Thread(target=self._worker, args=(w,), daemon=True)

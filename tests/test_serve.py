@@ -171,3 +171,26 @@ def test_mix_equals_alone():
             want = ctxs[r.dataset].iso(v).cpu().numpy()
             assert got.shape[0] == want.shape[0]
             assert (canonical(got.numpy()) == canonical(want)).all()
+
+
+@pytest.mark.gpu
+def test_preload_then_serve():
+    """preload() runs the dual-mesh pass of data sets in the given order while
+    they fit the budget; requests for them are then served without another."""
+    from paper_2004_08475_b300 import synth
+    from paper_2004_08475_b300.serve import Server
+    data = {"sphere": synth.sphere_tiny()[:4],
+            "rnd": synth.random_octree(6, levels=3, roots=4)[:4]}
+    srv = Server(budget_bytes=1 << 30, slots=2, keep_results=True, out_capacity=1 << 14)
+    for name, (x, l, s, iso) in data.items():
+        srv.add_dataset(name, x, l, s)
+    srv.preload(["rnd", "sphere"])
+    assert srv.stats["prefills"] == 2 and list(srv.resident) == ["rnd", "sphere"]
+    assert all(r.users == 0 and r.ctx is not None for r in srv.resident.values())
+    srv.start()
+    reqs = [srv.submit(name, [float(iso)]) for name, (x, l, s, iso) in data.items()]
+    for r in reqs:
+        assert r.done.wait(60)
+    srv.stop()
+    assert not any(r.error for r in reqs) and srv.stats["prefills"] == 2
+    assert all(r.counts[0] > 0 for r in reqs)
