@@ -1335,7 +1335,9 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
                                             const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
   extern __shared__ __align__(16) unsigned mc_smem[];
+  __shared__ unsigned short cell_tab[1 << (3 * LOGB)];
   load_mc(sh, mc);
+  fill_cell_table<LOGB>(cell_tab);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -1400,8 +1402,8 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
           if (KEYS) {
             reinterpret_cast<unsigned long long*>(wst)[q] = slot_pair(va, vb);
           } else {
-            const float3 p = edge_vertex(slot_cell<LOGB>(L.bricks, va), __ldg(L.scal + va),
-                                         slot_cell<LOGB>(L.bricks, vb), __ldg(L.scal + vb), iso);
+            const float3 p = edge_vertex(slot_cell_tab<LOGB>(L.bricks, cell_tab, va), __ldg(L.scal + va),
+                                         slot_cell_tab<LOGB>(L.bricks, cell_tab, vb), __ldg(L.scal + vb), iso);
             wst[3 * q] = p.x;
             wst[3 * q + 1] = p.y;
             wst[3 * q + 2] = p.z;
@@ -1556,13 +1558,15 @@ __global__ void __launch_bounds__(256) k_weld_index(const unsigned long long* __
 // a job is one data set's dual list with its run of iso-values, and every
 // (job, iso-value) pair owns one output segment. Three passes:
 //   k_batch_count: per tile, the kept triangles of every iso-value of its
-//     job (each dual's vertex slots and scalars read once for all values);
+//     job (each dual's vertex slots and scalars read once for all values,
+//     work only for the (dual, iso-value) pairs that cross);
 //   k_batch_scan: per segment, the exclusive prefix over the job's tiles
 //     (each tile's first row inside the segment) and the segment's total;
 //     k_batch_bases: the segments' first rows (the caller's offsets);
-//   k_batch_emit: per tile, the same cases again; each warp reserves its
-//     triangles of one iso-value inside the tile's run of that segment with
-//     a shared-memory atomic and writes them as one coalesced run.
+//   k_batch_emit: per tile, the same crossing pairs again; each pair
+//     reserves its triangles inside the tile's run of its segment with a
+//     shared-memory atomic, and the warp computes the listed triangles'
+//     vertices together and writes them to their rows.
 // No global atomics and no waiting: every tile knows where its triangles go.
 __device__ __forceinline__ int job_of_tile(const BatchTable& T, long long g) {
   int j = 0;
@@ -1574,52 +1578,85 @@ __device__ __forceinline__ int4 slot_cell_rt(const int4* __restrict__ bricks, un
   return logb == 3 ? slot_cell<3>(bricks, slot) : slot_cell<2>(bricks, slot);
 }
 
-// One dual per lane, 32 per warp step: its vertex slots and scalars, their
-// range, and whether its 8 vertices are 8 different cells.
-struct BatchDual {
-  unsigned v[8];
-  float s[8];
-  float mn, mx;
-  bool live, distinct;
+// The job's iso-values in increasing order, sorted once per tile. A dual
+// crosses iso (its case is neither 0 nor 255) exactly when
+// min(scalars) <= iso < max(scalars), so the values crossing it are one run
+// [below(min), below(max)) of the sorted list: the passes below visit only
+// (dual, iso-value) pairs that cross, spread evenly over the warp's lanes.
+struct BatchIsos {
+  float v[kMaxIso];             // sorted values (NaN last, ties by index)
+  unsigned char idx[kMaxIso];   // each one's index in the job's run
 };
 
-__device__ __forceinline__ void batch_load(const BatchJob& J, long long d, long long d_hi, BatchDual& b) {
-  b.live = d < d_hi;
-  b.distinct = false;
-  b.mn = 3.4e38f;
-  b.mx = -3.4e38f;
-  if (!b.live) return;
-  b.distinct = load_dual(J.duals, d, b.v);
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    b.s[e] = __ldg(J.scal + b.v[e]);
-    b.mn = fminf(b.mn, b.s[e]);
-    b.mx = fmaxf(b.mx, b.s[e]);
+__device__ __forceinline__ bool iso_before(float b, int j, float a, int k) {
+  if (b != b) return a != a && j < k;
+  return a != a || b < a || (b == a && j < k);
+}
+
+// S from the job's values iso[0..n) in shared memory (a rank per value).
+__device__ __forceinline__ void batch_sort_isos(const float* iso, int n, BatchIsos& S) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const float a = iso[k];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += iso_before(iso[j], j, a, k) ? 1 : 0;
+    S.v[r] = a;
+    S.idx[r] = (unsigned char)k;
   }
 }
 
-// Minimum and maximum of a float over the warp (dead lanes hold +-3.4e38).
-__device__ __forceinline__ float warp_min_f(float v) {
+// How many of the n sorted values lie below x (a NaN never does).
+__device__ __forceinline__ int batch_below(const BatchIsos& S, int n, float x) {
+  int lo = 0;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
-__device__ __forceinline__ float warp_max_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
+  for (int s = kMaxIso; s > 0; s >>= 1)
+    if (lo + s <= n && S.v[lo + s - 1] < x) lo += s;
+  return lo;
 }
 
-// Kept-triangle mask of the dual at `iso` (0 when no corner crosses); v:
-// its 8 vertex slots (registers or shared memory).
-__device__ __forceinline__ unsigned batch_keep(const BatchDual& b, const unsigned* v, float iso, const McShared& sh,
-                                               unsigned long long ea, unsigned long long eb, int& cas) {
-  cas = 0;
-  if (!b.live || !(b.mx > iso) || b.mn > iso) return 0u;   // case 0 or 255
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned x, int lane) {
 #pragma unroll
-  for (int e = 0; e < 8; ++e) cas |= (b.s[e] > iso ? 1 : 0) << e;
-  return kept_of(b.distinct, sh.packed[cas], sh.count[cas], v, ea, eb);
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
 }
+
+// The warp's pairs are numbered lane by lane (lane j owns [excl_j, excl_j +
+// n_j)); the owner of pair p is the last lane whose first pair is <= p.
+// Every lane of the warp takes part (the shuffles read other lanes' excl).
+__device__ __forceinline__ int pair_owner(unsigned excl, unsigned p) {
+  int src = 0;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const unsigned e = __shfl_sync(kFull, excl, src + s);
+    if (e <= p) src += s;
+  }
+  return src;
+}
+
+// Case index of a dual at iso from its 8 scalars s[e * stride].
+__device__ __forceinline__ int batch_case(const float* s, int stride, float iso) {
+  int cas = 0;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) cas |= (s[e * stride] > iso ? 1 : 0) << e;
+  return cas;
+}
+
+// Kept-triangle mask of a crossing dual: every triangle of its case when its
+// 8 vertices are 8 different cells, else the non-degenerate ones (slots
+// v[e * stride]).
+__device__ __forceinline__ unsigned batch_kept(bool distinct, int cas, const unsigned* v, int stride,
+                                               const McShared& sh, unsigned long long ea, unsigned long long eb) {
+  if (distinct) return (1u << sh.count[cas]) - 1u;
+  unsigned vv[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) vv[e] = v[e * stride];
+  return kept_triangles(sh.packed[cas], sh.count[cas], vv, ea, eb);
+}
+
+// Duals per warp step of k_batch_count (two per lane).
+constexpr int kCountStep = 64;
 
 __global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ BatchTable T,
                                                      const float* __restrict__ isos, unsigned* __restrict__ counts,
@@ -1627,34 +1664,81 @@ __global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ Bat
   __shared__ McShared sh;
   __shared__ unsigned cnt[kMaxIso];
   __shared__ float iso_sh[kMaxIso];
+  __shared__ BatchIsos S;
+  __shared__ unsigned wv[8][8][kCountStep];   // per warp: vertex slot e of dual i at [e][i]
+  __shared__ float wsc[8][8][kCountStep];     // and its scalar
   load_mc(sh, mc);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (long long g = blockIdx.x; g < T.n_tiles; g += gridDim.x) {
     const BatchJob& J = T.job[job_of_tile(T, g)];
     const long long t = g - J.tile0;
-    for (int k = threadIdx.x; k < J.n_iso; k += blockDim.x) {
+    const int n_iso = J.n_iso;
+    for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
       cnt[k] = 0;
       iso_sh[k] = __ldg(isos + J.q0 + k);
     }
     __syncthreads();
+    batch_sort_isos(iso_sh, n_iso, S);
+    __syncthreads();
     const long long d_hi = min(J.nd, (t + 1) * kBTile);
-    for (long long base = t * kBTile + 64 * w; base < d_hi; base += 64 * nw) {   // two duals per lane
-      BatchDual b0, b1;
-      batch_load(J, base + lane, d_hi, b0);
-      batch_load(J, base + 32 + lane, d_hi, b1);
-      // the warp's scalar range: iso-values outside it cross none of its duals
-      const float lo = warp_min_f(fminf(b0.mn, b1.mn)), hi = warp_max_f(fmaxf(b0.mx, b1.mx));
-      for (int k = 0; k < J.n_iso; ++k) {
-        if (!(hi > iso_sh[k]) || lo > iso_sh[k]) continue;   // uniform over the warp
-        int cas;
-        unsigned c = __popc(batch_keep(b0, b0.v, iso_sh[k], sh, mc.edge_a, mc.edge_b, cas));
-        c += __popc(batch_keep(b1, b1.v, iso_sh[k], sh, mc.edge_a, mc.edge_b, cas));
-        c = __reduce_add_sync(kFull, c);
-        if (lane == 0 && c) atomicAdd(&cnt[k], c);
+    for (long long base = t * kBTile + kCountStep * w; base < d_hi; base += kCountStep * nw) {
+      // duals lane and lane + 32 of the step: slots and scalars to shared
+      // memory, the run of sorted iso-values crossing each
+      int klo0 = 0, n0 = 0, klo1 = 0, n1 = 0;
+      unsigned dm0 = 0, dm1 = 0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const long long d = base + lane + 32 * j;
+        const int i = lane + 32 * j;
+        bool distinct = false;
+        int klo = 0, n = 0;
+        if (d < d_hi) {
+          unsigned v[8];
+          float s[8];
+          distinct = load_dual(J.duals, d, v);
+          float mn = 3.4e38f, mx = -3.4e38f;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            s[e] = __ldg(J.scal + v[e]);
+            mn = fminf(mn, s[e]);
+            mx = fmaxf(mx, s[e]);
+          }
+          klo = batch_below(S, n_iso, mn);
+          n = max(0, batch_below(S, n_iso, mx) - klo);
+          if (n > 0) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              wv[w][e][i] = v[e];
+              wsc[w][e][i] = s[e];
+            }
+          }
+        }
+        const unsigned dm = __ballot_sync(kFull, distinct);
+        if (j == 0) { klo0 = klo; n0 = n; dm0 = dm; } else { klo1 = klo; n1 = n; dm1 = dm; }
       }
+      const unsigned mine = (unsigned)(n0 + n1);
+      const unsigned incl = warp_incl_scan(mine, lane), excl = incl - mine;
+      const unsigned n_pairs = __shfl_sync(kFull, incl, 31);
+      __syncwarp();
+      for (unsigned p0 = 0; p0 < n_pairs; p0 += 32) {
+        const unsigned p = p0 + lane;
+        const int src = pair_owner(excl, p);
+        const int r = (int)(p - __shfl_sync(kFull, excl, src));
+        const int sn0 = __shfl_sync(kFull, n0, src);
+        const int slo0 = __shfl_sync(kFull, klo0, src), slo1 = __shfl_sync(kFull, klo1, src);
+        if (p >= n_pairs) continue;   // no shuffles below
+        const bool second = r >= sn0;
+        const int i = src + (second ? 32 : 0);
+        const int ks = second ? slo1 + r - sn0 : slo0 + r;
+        const int cas = batch_case(&wsc[w][0][i], kCountStep, S.v[ks]);
+        const unsigned keep = batch_kept((((second ? dm1 : dm0) >> src) & 1u) != 0, cas, &wv[w][0][i], kCountStep,
+                                         sh, mc.edge_a, mc.edge_b);
+        if (keep) atomicAdd(&cnt[S.idx[ks]], (unsigned)__popc(keep));
+      }
+      __syncwarp();
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < J.n_iso; k += blockDim.x) counts[J.cbase + k * J.tiles + t] = cnt[k];
+    for (int k = threadIdx.x; k < n_iso; k += blockDim.x) counts[J.cbase + k * J.tiles + t] = cnt[k];
     __syncthreads();
   }
 }
@@ -1729,27 +1813,28 @@ __global__ void k_batch_bases(int n_q, const long long* totals, long long* off) 
   off[n_q] = run;
 }
 
-// Per dual of the emit pass (one per lane of a warp step), computed once for
-// all iso-values: each vertex cell's centre (the fp32 operations of
-// edge_vertex) and scalar, and per hexahedron edge whether its endpoints
-// swap (the upper corner's cell lies lower in (z, y, x) order).
-struct BatchVerts {
-  float4 c[8];        // centre x, y, z and scalar of vertex e
-  unsigned v[8];      // vertex slots
-  unsigned swap;      // bit k: edge k's vertex b comes first
-  unsigned pad[3];
+// Per warp of k_batch_emit, the 32 duals of a warp step, by (vertex, dual):
+// vertex e of dual i at [e][i], so that lanes reading one vertex of
+// different duals meet in different banks (the float4 rows carry one entry
+// of padding: lanes reading vertex e of dual i and vertex e' of dual i'
+// share a bank group only when e + i == e' + i' mod 8).
+struct BatchWarp {
+  float4 c[8][33];     // centre x, y, z and scalar (the fp32 operations of edge_vertex)
+  float s[8][32];      // the scalars again, for the case loop
+  unsigned v[8][32];   // vertex slots
+  unsigned swap[32];   // bit k: edge k's vertex b lies lower in (z, y, x) order
 };
-// Triangles a warp lists per step over all its iso-values before computing
-// their vertices (one iso-value adds at most 32 duals x 5 triangles).
+// Triangles a warp lists before computing their vertices (one round of 32
+// pairs adds at most 32 x 5).
 constexpr int kBatchList = 256;
 
-__device__ __forceinline__ float3 batch_vertex(const BatchVerts& d, int k, unsigned long long ea, unsigned long long eb,
-                                               float iso) {
+__device__ __forceinline__ float3 batch_vertex(const BatchWarp& W, int i, int k, unsigned long long ea,
+                                               unsigned long long eb, float iso) {
   int a = (int)((ea >> (4 * k)) & 15), b = (int)((eb >> (4 * k)) & 15);
-  if ((d.swap >> k) & 1u) {
+  if ((W.swap[i] >> k) & 1u) {
     const int t = a; a = b; b = t;
   }
-  const float4 pa = d.c[a], pb = d.c[b];
+  const float4 pa = W.c[a][i], pb = W.c[b][i];
   const float t = __fdiv_rn(__fsub_rn(iso, pa.w), __fsub_rn(pb.w, pa.w));
   return make_float3(__fadd_rn(pa.x, __fmul_rn(t, __fsub_rn(pb.x, pa.x))),
                      __fadd_rn(pa.y, __fmul_rn(t, __fsub_rn(pb.y, pa.y))),
@@ -1757,18 +1842,18 @@ __device__ __forceinline__ float3 batch_vertex(const BatchVerts& d, int k, unsig
 }
 
 // List entry of k_batch_emit: the triangle's row inside its tile's run of
-// its segment (bits 0-31), the lane whose dual it belongs to (32-36), the
-// iso-value (37-42) and its three edge ids (43-54).
+// its segment (bits 0-31), the dual's lane (32-36), the iso-value's index in
+// the job's run (37-42) and the triangle's three edge ids (43-54).
 __device__ __forceinline__ unsigned long long batch_entry(unsigned row, unsigned lane, unsigned k, unsigned edges) {
   return (unsigned long long)row | ((unsigned long long)lane << 32) | ((unsigned long long)k << 37) |
          ((unsigned long long)edges << 43);
 }
 
 // The warp's listed triangles, one vertex per lane in turn: interpolated
-// from the listing lane's vertex data and written straight to its row (a
-// run of consecutive rows per segment, so consecutive lanes write
-// consecutive 12-byte vertices).
-__device__ __forceinline__ void batch_flush(const unsigned long long* lst, unsigned len, const BatchVerts* wverts,
+// from the dual's vertex data and written straight to its row (a run of
+// consecutive rows per segment, so consecutive lanes write consecutive
+// 12-byte vertices).
+__device__ __forceinline__ void batch_flush(const unsigned long long* lst, unsigned len, const BatchWarp& W,
                                             const float* iso_sh, const long long* row0, const long long* rowend,
                                             float* __restrict__ tris, unsigned long long ea, unsigned long long eb) {
   for (unsigned q = threadIdx.x & 31; q < 3u * len; q += 32) {
@@ -1777,7 +1862,7 @@ __device__ __forceinline__ void batch_flush(const unsigned long long* lst, unsig
     const unsigned k = (unsigned)(ent >> 37) & 63u;
     const long long row = row0[k] + (long long)(unsigned)ent;
     if (row >= rowend[k]) continue;   // capacity: exact prefix only
-    const float3 p = batch_vertex(wverts[(ent >> 32) & 31u], (int)((ent >> (43 + 4 * c)) & 15u), ea, eb, iso_sh[k]);
+    const float3 p = batch_vertex(W, (int)((ent >> 32) & 31u), (int)((ent >> (43 + 4 * c)) & 15u), ea, eb, iso_sh[k]);
     float* out = tris + 9 * row + 3 * c;
     out[0] = p.x;
     out[1] = p.y;
@@ -1795,110 +1880,112 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
   __shared__ float iso_sh[kMaxIso];
   __shared__ long long row0[kMaxIso];       // the tile's first row, per iso-value
   __shared__ long long rowend[kMaxIso];     // end of the segment's rows that fit the buffer
-  __shared__ BatchVerts verts[256];         // each lane's dual
+  __shared__ BatchIsos S;
+  __shared__ BatchWarp wdata[8];
   __shared__ unsigned long long tlist[8][kBatchList];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   unsigned long long* lst = tlist[w];
-  BatchVerts& mine_v = verts[threadIdx.x];
+  BatchWarp& W = wdata[w];
   load_mc(sh, mc);
   for (long long g = blockIdx.x; g < T.n_tiles; g += gridDim.x) {
     const BatchJob& J = T.job[job_of_tile(T, g)];
     const long long t = g - J.tile0;
-    for (int k = threadIdx.x; k < J.n_iso; k += blockDim.x) {
+    const int n_iso = J.n_iso;
+    for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
       tcnt[k] = 0;
       iso_sh[k] = __ldg(isos + J.q0 + k);
       row0[k] = __ldg(off + J.q0 + k) + __ldg(rel + J.cbase + k * J.tiles + t);
       rowend[k] = min(__ldg(off + J.q0 + k + 1), total_cap);
     }
     __syncthreads();
-    float lo_iso = 3.4e38f, hi_iso = -3.4e38f;   // range of the job's iso-values
-    for (int k = 0; k < J.n_iso; ++k) {
-      lo_iso = fminf(lo_iso, iso_sh[k]);
-      hi_iso = fmaxf(hi_iso, iso_sh[k]);
-    }
+    batch_sort_isos(iso_sh, n_iso, S);
+    __syncthreads();
     const long long d_hi = min(J.nd, (t + 1) * kBTile);
     for (long long base = t * kBTile + 32 * w; base < d_hi; base += 32 * nw) {
-      BatchDual b;   // (its slots go to shared memory, the scalars stay in registers)
-      {
-        const long long d = base + lane;
-        b.live = d < d_hi;
-        b.distinct = false;
-        b.mn = 3.4e38f;
-        b.mx = -3.4e38f;
-        if (b.live) {
-          unsigned v[8];
-          b.distinct = load_dual(J.duals, d, v);
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            mine_v.v[e] = v[e];
-            b.s[e] = __ldg(J.scal + v[e]);
-            b.mn = fminf(b.mn, b.s[e]);
-            b.mx = fmaxf(b.mx, b.s[e]);
-          }
-        }
-      }
-      if (b.live && b.mx > lo_iso && !(b.mn > hi_iso)) {   // some iso-value may cross it: its vertex data
-        // (z, y, x) order of the vertex cells' corners as one 64-bit key each:
-        // corners relative to vertex 0's, which they differ from by less
-        // than 2^16 per axis (every vertex cell holds a point within one
-        // cell width of the dual's owner)
-        unsigned long long key[8];
-        int4 c0 = make_int4(0, 0, 0, 0);
+      const long long d = base + lane;
+      bool distinct = false;
+      int klo = 0, n = 0;
+      if (d < d_hi) {
+        unsigned v[8];
+        float s[8];
+        distinct = load_dual(J.duals, d, v);
+        float mn = 3.4e38f, mx = -3.4e38f;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int4 cr = slot_cell_rt(J.bricks, mine_v.v[e], J.logb);
-          if (e == 0) c0 = cr;
-          const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
-          mine_v.c[e] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
-                                    __fadd_rn(__int2float_rn(cr.z), h), b.s[e]);
-          key[e] = ((unsigned long long)(unsigned)(cr.z - c0.z + 65536) << 34) |
-                   ((unsigned long long)(unsigned)(cr.y - c0.y + 65536) << 17) | (unsigned)(cr.x - c0.x + 65536);
+          s[e] = __ldg(J.scal + v[e]);
+          mn = fminf(mn, s[e]);
+          mx = fmaxf(mx, s[e]);
         }
-        // the hexahedron's 12 edges (a, b), a < b, in increasing order: the
-        // numbering the case table's edge ids use
-        constexpr int kEa[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6};
-        constexpr int kEb[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
-        unsigned sw = 0;
+        klo = batch_below(S, n_iso, mn);
+        n = max(0, batch_below(S, n_iso, mx) - klo);
+        if (n > 0) {   // some iso-value crosses it: its vertex data, once for all of them
+          // (z, y, x) order of the vertex cells' corners as one 64-bit key
+          // each, relative to vertex 0's corner, which they differ from by
+          // less than 2^16 per axis (every vertex cell holds a point within
+          // one cell width of the dual's owner)
+          unsigned long long key[8];
+          int4 c0 = make_int4(0, 0, 0, 0);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) sw |= (key[kEb[k]] < key[kEa[k]] ? 1u : 0u) << k;
-        mine_v.swap = sw;
+          for (int e = 0; e < 8; ++e) {
+            const int4 cr = slot_cell_rt(J.bricks, v[e], J.logb);
+            if (e == 0) c0 = cr;
+            const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
+            W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
+                                       __fadd_rn(__int2float_rn(cr.z), h), s[e]);
+            W.s[e][lane] = s[e];
+            W.v[e][lane] = v[e];
+            key[e] = ((unsigned long long)(unsigned)(cr.z - c0.z + 65536) << 34) |
+                     ((unsigned long long)(unsigned)(cr.y - c0.y + 65536) << 17) | (unsigned)(cr.x - c0.x + 65536);
+          }
+          // the hexahedron's 12 edges (a, b), a < b, in increasing order: the
+          // numbering the case table's edge ids use
+          constexpr int kEa[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6};
+          constexpr int kEb[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
+          unsigned sw = 0;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) sw |= (key[kEb[k]] < key[kEa[k]] ? 1u : 0u) << k;
+          W.swap[lane] = sw;
+        }
       }
+      const unsigned dmask = __ballot_sync(kFull, distinct);
+      const unsigned incl = warp_incl_scan((unsigned)n, lane), excl = incl - (unsigned)n;
+      const unsigned n_pairs = __shfl_sync(kFull, incl, 31);
       __syncwarp();
-      // the warp's scalar range: iso-values outside it cross none of its duals
-      const float lo = warp_min_f(b.mn), hi = warp_max_f(b.mx);
       unsigned len = 0;   // entries in the warp's list
-      for (int k = 0; k < J.n_iso; ++k) {
-        const float iso = iso_sh[k];
-        if (!(hi > iso) || lo > iso) continue;   // uniform over the warp
-        int cas;
-        const unsigned keep = batch_keep(b, mine_v.v, iso, sh, mc.edge_a, mc.edge_b, cas);
-        const unsigned mine = __popc(keep);
-        unsigned incl = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
+      for (unsigned p0 = 0; p0 < n_pairs; p0 += 32) {
+        const unsigned p = p0 + lane;
+        const int src = pair_owner(excl, p);
+        const int ks = __shfl_sync(kFull, klo, src) + (int)(p - __shfl_sync(kFull, excl, src));
+        const bool live = p < n_pairs;
+        unsigned keep = 0, kk = 0;
+        int cas = 0;
+        if (live) {
+          kk = S.idx[ks];
+          cas = batch_case(&W.s[0][src], 32, S.v[ks]);
+          keep = batch_kept(((dmask >> src) & 1u) != 0, cas, &W.v[0][src], 32, sh, mc.edge_a, mc.edge_b);
         }
-        const unsigned total = __shfl_sync(kFull, incl, 31);
+        const unsigned c = __popc(keep);
+        const unsigned ci = warp_incl_scan(c, lane);
+        const unsigned total = __shfl_sync(kFull, ci, 31);
         if (total == 0) continue;
         if (len + total > (unsigned)kBatchList) {   // list full: its vertices first
           __syncwarp();
-          batch_flush(lst, len, verts + w * 32, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
+          batch_flush(lst, len, W, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
           __syncwarp();
           len = 0;
         }
-        unsigned p0 = 0;
-        if (lane == 0) p0 = atomicAdd(&tcnt[k], total);   // rows inside the tile's run of segment k
-        p0 = __shfl_sync(kFull, p0, 0);
-        unsigned pos = len + incl - mine, row = p0 + incl - mine;
-        const unsigned long long pk = sh.packed[cas];
-        for (int tt = 0; tt < 5; ++tt)
-          if ((keep >> tt) & 1u)
-            lst[pos++] = batch_entry(row++, (unsigned)lane, (unsigned)k, (unsigned)(pk >> (12 * tt)) & 0xFFFu);
+        if (c) {
+          unsigned row = atomicAdd(&tcnt[kk], c);   // rows inside the tile's run of segment kk
+          unsigned pos = len + ci - c;
+          const unsigned long long pk = sh.packed[cas];
+          for (int tt = 0; tt < 5; ++tt)
+            if ((keep >> tt) & 1u)
+              lst[pos++] = batch_entry(row++, (unsigned)src, kk, (unsigned)(pk >> (12 * tt)) & 0xFFFu);
+        }
         len += total;
       }
       __syncwarp();
-      batch_flush(lst, len, verts + w * 32, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
+      batch_flush(lst, len, W, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
       __syncwarp();
     }
     __syncthreads();
