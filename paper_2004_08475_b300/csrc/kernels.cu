@@ -140,14 +140,24 @@ __device__ __forceinline__ int4 slot_cell_tab(const int4* __restrict__ bricks, c
 
 constexpr int kUnroll = 4;   // cells per lane per trip of the cell-parallel loops
 
+// The home sector of a probe, entries h and h + 1 (h even, the table 32-byte
+// aligned), in one 32-byte load.
+__device__ __forceinline__ void load_home_sector(const ulonglong2* p, ulonglong2& a, ulonglong2& b) {
+  asm("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(a.x), "=l"(a.y), "=l"(b.x), "=l"(b.y)
+      : "l"(p));
+}
+
 // Pass 1 over the cells: validate corners and levels, take the bounding box
 // and the deepest level, and insert every cell's brick key into the hash
 // table (scalars are checked in pass 2). The CAS winner of a key numbers the
-// brick and records its corner and level. Each lane takes kUnroll cells per
-// trip, loads and first probes hoisted, so that their memory latencies
-// overlap; the first probe reads the home sector's two entries whole (key
-// and brick index). Lanes holding the same key simply both find it (or race
-// on one CAS, which one of them wins).
+// brick and records its corner and level. Each lane takes kUnroll = 4
+// consecutive cells per trip (their corners as three 16-byte loads and
+// their levels as one 4-byte load when the arrays are aligned for it), loads
+// and first probes hoisted, so that their memory latencies overlap; the
+// first probe reads the home sector's two entries whole (keys and brick
+// indices) in one load. Lanes holding the same key simply both find it (or
+// race on one CAS, which one of them wins).
 // codes (binned placement): per cell its slot (brick index << 3 LOGB | its
 // Morton index in the brick) when the brick's index was already readable,
 // else kCodeEntry | its brick's table entry << 3 LOGB | Morton index (the
@@ -170,20 +180,37 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
   unsigned err = 0;
   // a table this crowded is rebuilt larger by the host: fail fast
   const unsigned long long limit = hmask < 4095ull ? hmask + 1 : 4096ull;
+  static_assert(kUnroll == 4, "a lane's cells are read as one 4-byte load of levels");
+  const bool vec = ((reinterpret_cast<uintptr_t>(xyz) & 15u) | (reinterpret_cast<uintptr_t>(lvl) & 3u) |
+                    (reinterpret_cast<uintptr_t>(codes) & 15u)) == 0;
   int trip = 0;
   for (long long base = wid * 32 * kUnroll; base < n; base += nwarps * 32 * kUnroll) {
     if ((trip++ & 31) == 0 && __any_sync(kFull, (__ldcg(&sc->err) & ERR_HASH_FULL) != 0u)) break;
     int x[kUnroll], y[kUnroll], z[kUnroll], l[kUnroll];
+    const long long c0 = base + kUnroll * lane;   // the lane's first cell
+    const bool whole = vec && c0 + kUnroll <= n;
+    if (whole) {   // streamed once: evict first, keep the hash table in L2
+      const int4* p = reinterpret_cast<const int4*>(xyz + 3 * c0);
+      const int4 a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
+      const unsigned lv = __ldcs(reinterpret_cast<const unsigned*>(lvl + c0));
+      x[0] = a.x; y[0] = a.y; z[0] = a.z;
+      x[1] = a.w; y[1] = b.x; z[1] = b.y;
+      x[2] = b.z; y[2] = b.w; z[2] = c.x;
+      x[3] = c.y; y[3] = c.z; z[3] = c.w;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const long long i = base + u * 32 + lane;
-      x[u] = y[u] = z[u] = 0;
-      l[u] = -1;
-      if (i < n) {   // streamed once: evict first, keep the hash table in L2
-        x[u] = __ldcs(xyz + 3 * i);
-        y[u] = __ldcs(xyz + 3 * i + 1);
-        z[u] = __ldcs(xyz + 3 * i + 2);
-        l[u] = __ldcs(lvl + i);
+      for (int u = 0; u < kUnroll; ++u) l[u] = (int)((lv >> (8 * u)) & 255u);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long i = c0 + u;
+        x[u] = y[u] = z[u] = 0;
+        l[u] = -1;
+        if (i < n) {
+          x[u] = __ldcs(xyz + 3 * i);
+          y[u] = __ldcs(xyz + 3 * i + 1);
+          z[u] = __ldcs(xyz + 3 * i + 2);
+          l[u] = __ldcs(lvl + i);
+        }
       }
     }
     unsigned long long key[kUnroll];
@@ -217,13 +244,20 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
         }
       }
       // independent first probes: the home sector (entry h whole, entry h + 1's key)
-      e0[u] = key[u] != kEmptyKey ? __ldcg(htab + h[u]) : make_ulonglong2(0ull, 0ull);
-      cur1[u] = key[u] != kEmptyKey ? __ldcg(&htab[h[u] + 1].x) : 0ull;
+      e0[u] = make_ulonglong2(0ull, 0ull);
+      cur1[u] = 0ull;
+      if (key[u] != kEmptyKey) {
+        ulonglong2 e1;
+        load_home_sector(htab + h[u], e0[u], e1);
+        cur1[u] = e1.x;
+      }
     }
+    unsigned code4[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
+      code4[u] = kReject;
       if (key[u] == kEmptyKey) continue;
-      const long long i = base + u * 32 + lane;
+      const long long i = c0 + u;
       unsigned code;
       if (e0[u].x == key[u]) {   // at home, the common case: the brick index came with the key
         code = e0[u].y != kEmptyKey ? ((unsigned)e0[u].y << (3 * LOGB)) | loc[u]
@@ -260,8 +294,12 @@ __global__ void __launch_bounds__(1024) k_insert_bricks(
         if (!done) err |= ERR_HASH_FULL;
         else if (code == kReject) code = kCodeEntry | ((unsigned)hh << (3 * LOGB)) | loc[u];
       }
-      if (codes) __stcs(codes + i, code);
+      code4[u] = code;
+      if (codes && !whole) __stcs(codes + i, code);
     }
+    // (an invalid cell's code is never read: the host stops on its error)
+    if (codes && whole)
+      __stcs(reinterpret_cast<uint4*>(codes + c0), make_uint4(code4[0], code4[1], code4[2], code4[3]));
   }
   // block reduction, then one set of atomics per block
   __shared__ int red[8][32];
@@ -449,7 +487,7 @@ __device__ __forceinline__ unsigned scan_and_reserve(unsigned* cnt, unsigned* gb
 // A cell's slot is its code (from k_insert_bricks), or one table read away
 // when the code holds the table entry of its brick instead.
 template <int LOGB>
-__global__ void __launch_bounds__(kCoarseThreads) k_bin_coarse(const float* __restrict__ s, long long n, Locator L,
+__global__ void __launch_bounds__(kCoarseThreads, 3) k_bin_coarse(const float* __restrict__ s, long long n, Locator L,
                                                                int n_coarse, Stage A,
                                                                unsigned* __restrict__ coarse_count, Scratch* sc,
                                                                const unsigned* __restrict__ codes) {

@@ -205,6 +205,35 @@ def test_host_pointer_upload():
     compare(g, o, _extent(info))
 
 
+@pytest.mark.parametrize("part", [-1, 1])
+def test_misaligned_device_arrays(part):
+    """Cell arrays that start one cell into their allocations (corners 12
+    bytes, levels 1 byte past an aligned address, so the insert pass reads
+    them cell by cell instead of in 16-byte groups), with a cell count that
+    leaves a ragged last group: the oracle's result on both placement paths."""
+    from paper_2004_08475_b300 import amriso
+    xyz, lv, s, iso, info = synth.random_octree(78, levels=4, roots=5, p_split=0.45, p_hole=0.05)
+    n = xyz.shape[0] - 3 if (xyz.shape[0] - 3) % 4 else xyz.shape[0] - 2   # not a multiple of 4
+    xb = torch.zeros((n + 1, 3), dtype=torch.int32, device="cuda")
+    lb = torch.zeros(n + 1, dtype=torch.uint8, device="cuda")
+    sb = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    xb[1:] = xyz[:n].cuda()
+    lb[1:] = lv[:n].cuda()
+    sb[1:] = s[:n].cuda()
+    x1, l1, s1 = xb[1:], lb[1:], sb[1:]
+    assert x1.data_ptr() % 16 and l1.data_ptr() % 4
+    ctx = amriso.AmrContext()
+    ctx.upload(x1, l1, s1)
+    ctx.build_locator(partitioned=part)
+    ctx.dual_cells()
+    cases, ntri = ctx.iso_cases(iso)
+    g = {"duals": ctx.get_duals().cpu().numpy().astype(np.int64), "cases": cases.cpu().numpy(),
+         "ntri": ntri.cpu().numpy(), "tris": ctx.iso(iso).cpu().numpy()}
+    ctx.close()
+    r = compare(g, run_oracle(xyz[:n], lv[:n], s[:n], iso), _extent(info))
+    assert r["bit_exact_frac"] == 1.0
+
+
 def test_empty_and_single():
     from paper_2004_08475_b300 import amriso
     ctx = amriso.AmrContext()
