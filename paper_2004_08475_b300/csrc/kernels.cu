@@ -1612,10 +1612,6 @@ __device__ __forceinline__ int job_of_tile(const BatchTable& T, long long g) {
   return j;
 }
 
-__device__ __forceinline__ int4 slot_cell_rt(const int4* __restrict__ bricks, unsigned slot, int logb) {
-  return logb == 3 ? slot_cell<3>(bricks, slot) : slot_cell<2>(bricks, slot);
-}
-
 // The job's iso-values in increasing order, sorted once per tile. A dual
 // crosses iso (its case is neither 0 nor 255) exactly when
 // min(scalars) <= iso < max(scalars), so the values crossing it are one run
@@ -1631,12 +1627,13 @@ __device__ __forceinline__ bool iso_before(float b, int j, float a, int k) {
   return a != a || b < a || (b == a && j < k);
 }
 
-// S from the job's values iso[0..n) in shared memory (a rank per value).
-__device__ __forceinline__ void batch_sort_isos(const float* iso, int n, BatchIsos& S) {
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const float a = iso[k];
+// S from the job's values iso[0..n) (a rank per value), by the lanes of one
+// warp.
+__device__ __forceinline__ void batch_sort_isos(const float* __restrict__ iso, int n, BatchIsos& S) {
+  for (int k = threadIdx.x & 31; k < n; k += 32) {
+    const float a = __ldg(iso + k);
     int r = 0;
-    for (int j = 0; j < n; ++j) r += iso_before(iso[j], j, a, k) ? 1 : 0;
+    for (int j = 0; j < n; ++j) r += iso_before(__ldg(iso + j), j, a, k) ? 1 : 0;
     S.v[r] = a;
     S.idx[r] = (unsigned char)k;
   }
@@ -1696,30 +1693,35 @@ __device__ __forceinline__ unsigned batch_kept(bool distinct, int cas, const uns
 // Duals per warp step of k_batch_count (two per lane).
 constexpr int kCountStep = 64;
 
-__global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ BatchTable T,
+// A tile's iso-values and counters in k_batch_count: tiles are handed to
+// warps, so that a warp never waits for the other warps of its CTA.
+struct CountTile {
+  BatchIsos S;
+  unsigned cnt[kMaxIso];   // by position in S
+};
+
+__global__ void __launch_bounds__(256, 5) k_batch_count(const __grid_constant__ BatchTable T,
                                                      const float* __restrict__ isos, unsigned* __restrict__ counts,
                                                      const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
-  __shared__ unsigned cnt[kMaxIso];
-  __shared__ float iso_sh[kMaxIso];
-  __shared__ BatchIsos S;
+  __shared__ CountTile tiles[8];
   __shared__ unsigned wv[8][8][kCountStep];   // per warp: vertex slot e of dual i at [e][i]
   __shared__ float wsc[8][8][kCountStep];     // and its scalar
   load_mc(sh, mc);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (long long g = blockIdx.x; g < T.n_tiles; g += gridDim.x) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  CountTile& C = tiles[w];
+  const BatchIsos& S = C.S;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + w; g < T.n_tiles; g += nwarps) {
     const BatchJob& J = T.job[job_of_tile(T, g)];
     const long long t = g - J.tile0;
     const int n_iso = J.n_iso;
-    for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
-      cnt[k] = 0;
-      iso_sh[k] = __ldg(isos + J.q0 + k);
-    }
-    __syncthreads();
-    batch_sort_isos(iso_sh, n_iso, S);
-    __syncthreads();
+    for (int k = lane; k < n_iso; k += 32) C.cnt[k] = 0;
+    batch_sort_isos(isos + J.q0, n_iso, C.S);
+    __syncwarp();
     const long long d_hi = min(J.nd, (t + 1) * kBTile);
-    for (long long base = t * kBTile + kCountStep * w; base < d_hi; base += kCountStep * nw) {
+    for (long long base = t * kBTile; base < d_hi; base += kCountStep) {
       // duals lane and lane + 32 of the step: slots and scalars to shared
       // memory, the run of sorted iso-values crossing each
       int klo0 = 0, n0 = 0, klo1 = 0, n1 = 0;
@@ -1732,14 +1734,14 @@ __global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ Bat
         int klo = 0, n = 0;
         if (d < d_hi) {
           unsigned v[8];
-          float s[8];
+          float sv[8];
           distinct = load_dual(J.duals, d, v);
           float mn = 3.4e38f, mx = -3.4e38f;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            s[e] = __ldg(J.scal + v[e]);
-            mn = fminf(mn, s[e]);
-            mx = fmaxf(mx, s[e]);
+            sv[e] = __ldg(J.scal + v[e]);
+            mn = fminf(mn, sv[e]);
+            mx = fmaxf(mx, sv[e]);
           }
           klo = batch_below(S, n_iso, mn);
           n = max(0, batch_below(S, n_iso, mx) - klo);
@@ -1747,7 +1749,7 @@ __global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ Bat
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               wv[w][e][i] = v[e];
-              wsc[w][e][i] = s[e];
+              wsc[w][e][i] = sv[e];
             }
           }
         }
@@ -1771,13 +1773,12 @@ __global__ void __launch_bounds__(256) k_batch_count(const __grid_constant__ Bat
         const int cas = batch_case(&wsc[w][0][i], kCountStep, S.v[ks]);
         const unsigned keep = batch_kept((((second ? dm1 : dm0) >> src) & 1u) != 0, cas, &wv[w][0][i], kCountStep,
                                          sh, mc.edge_a, mc.edge_b);
-        if (keep) atomicAdd(&cnt[S.idx[ks]], (unsigned)__popc(keep));
+        if (keep) atomicAdd(&C.cnt[ks], (unsigned)__popc(keep));
       }
       __syncwarp();
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < n_iso; k += blockDim.x) counts[J.cbase + k * J.tiles + t] = cnt[k];
-    __syncthreads();
+    for (int k = lane; k < n_iso; k += 32) counts[J.cbase + (long long)S.idx[k] * J.tiles + t] = C.cnt[k];
+    __syncwarp();
   }
 }
 
@@ -1859,12 +1860,19 @@ __global__ void k_batch_bases(int n_q, const long long* totals, long long* off) 
 struct BatchWarp {
   float4 c[8][33];     // centre x, y, z and scalar (the fp32 operations of edge_vertex)
   float s[8][32];      // the scalars again, for the case loop
-  unsigned v[8][32];   // vertex slots
   unsigned swap[32];   // bit k: edge k's vertex b lies lower in (z, y, x) order
+};
+// A tile's iso-values and rows in k_batch_emit: tiles are handed to warps,
+// so that a warp never waits for the other warps of its CTA.
+struct EmitTile {           // per iso-value, by position in S:
+  BatchIsos S;
+  unsigned tcnt[kMaxIso];      // rows of the tile taken so far
+  long long row0[kMaxIso];     // the tile's first row
+  long long rowend[kMaxIso];   // end of the segment's rows that fit the buffer
 };
 // Triangles a warp lists before computing their vertices (one round of 32
 // pairs adds at most 32 x 5).
-constexpr int kBatchList = 256;
+constexpr int kBatchList = 224;
 
 __device__ __forceinline__ float3 batch_vertex(const BatchWarp& W, int i, int k, unsigned long long ea,
                                                unsigned long long eb, float iso) {
@@ -1880,8 +1888,9 @@ __device__ __forceinline__ float3 batch_vertex(const BatchWarp& W, int i, int k,
 }
 
 // List entry of k_batch_emit: the triangle's row inside its tile's run of
-// its segment (bits 0-31), the dual's lane (32-36), the iso-value's index in
-// the job's run (37-42) and the triangle's three edge ids (43-54).
+// its segment (bits 0-31), the dual's lane (32-36), the iso-value's position
+// among the job's sorted values (37-42) and the triangle's three edge ids
+// (43-54).
 __device__ __forceinline__ unsigned long long batch_entry(unsigned row, unsigned lane, unsigned k, unsigned edges) {
   return (unsigned long long)row | ((unsigned long long)lane << 32) | ((unsigned long long)k << 37) |
          ((unsigned long long)edges << 43);
@@ -1892,15 +1901,15 @@ __device__ __forceinline__ unsigned long long batch_entry(unsigned row, unsigned
 // consecutive rows per segment, so consecutive lanes write consecutive
 // 12-byte vertices).
 __device__ __forceinline__ void batch_flush(const unsigned long long* lst, unsigned len, const BatchWarp& W,
-                                            const float* iso_sh, const long long* row0, const long long* rowend,
-                                            float* __restrict__ tris, unsigned long long ea, unsigned long long eb) {
+                                            const EmitTile& E, float* __restrict__ tris, unsigned long long ea,
+                                            unsigned long long eb) {
   for (unsigned q = threadIdx.x & 31; q < 3u * len; q += 32) {
     const unsigned e = q / 3u, c = q - 3u * e;
     const unsigned long long ent = lst[e];
     const unsigned k = (unsigned)(ent >> 37) & 63u;
-    const long long row = row0[k] + (long long)(unsigned)ent;
-    if (row >= rowend[k]) continue;   // capacity: exact prefix only
-    const float3 p = batch_vertex(W, (int)((ent >> 32) & 31u), (int)((ent >> (43 + 4 * c)) & 15u), ea, eb, iso_sh[k]);
+    const long long row = E.row0[k] + (long long)(unsigned)ent;
+    if (row >= E.rowend[k]) continue;   // capacity: exact prefix only
+    const float3 p = batch_vertex(W, (int)((ent >> 32) & 31u), (int)((ent >> (43 + 4 * c)) & 15u), ea, eb, E.S.v[k]);
     float* out = tris + 9 * row + 3 * c;
     out[0] = p.x;
     out[1] = p.y;
@@ -1914,45 +1923,48 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
                                                     const long long* __restrict__ off, float* __restrict__ tris,
                                                     long long total_cap, const __grid_constant__ McConst mc) {
   __shared__ McShared sh;
-  __shared__ unsigned tcnt[kMaxIso];        // rows of the tile taken so far, per iso-value
-  __shared__ float iso_sh[kMaxIso];
-  __shared__ long long row0[kMaxIso];       // the tile's first row, per iso-value
-  __shared__ long long rowend[kMaxIso];     // end of the segment's rows that fit the buffer
-  __shared__ BatchIsos S;
+  __shared__ unsigned short cell_tab3[1 << 9], cell_tab2[1 << 6];
+  __shared__ EmitTile tiles[8];
   __shared__ BatchWarp wdata[8];
   __shared__ unsigned long long tlist[8][kBatchList];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned long long* lst = tlist[w];
   BatchWarp& W = wdata[w];
+  EmitTile& E = tiles[w];
   load_mc(sh, mc);
-  for (long long g = blockIdx.x; g < T.n_tiles; g += gridDim.x) {
+  fill_cell_table<3>(cell_tab3);
+  fill_cell_table<2>(cell_tab2);
+  __syncthreads();
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + w; g < T.n_tiles; g += nwarps) {
     const BatchJob& J = T.job[job_of_tile(T, g)];
     const long long t = g - J.tile0;
     const int n_iso = J.n_iso;
-    for (int k = threadIdx.x; k < n_iso; k += blockDim.x) {
-      tcnt[k] = 0;
-      iso_sh[k] = __ldg(isos + J.q0 + k);
-      row0[k] = __ldg(off + J.q0 + k) + __ldg(rel + J.cbase + k * J.tiles + t);
-      rowend[k] = min(__ldg(off + J.q0 + k + 1), total_cap);
+    batch_sort_isos(isos + J.q0, n_iso, E.S);
+    __syncwarp();
+    const BatchIsos& S = E.S;
+    for (int ks = lane; ks < n_iso; ks += 32) {
+      const int k = S.idx[ks];
+      E.tcnt[ks] = 0;
+      E.row0[ks] = __ldg(off + J.q0 + k) + __ldg(rel + J.cbase + (long long)k * J.tiles + t);
+      E.rowend[ks] = min(__ldg(off + J.q0 + k + 1), total_cap);
     }
-    __syncthreads();
-    batch_sort_isos(iso_sh, n_iso, S);
-    __syncthreads();
+    __syncwarp();
     const long long d_hi = min(J.nd, (t + 1) * kBTile);
-    for (long long base = t * kBTile + 32 * w; base < d_hi; base += 32 * nw) {
+    for (long long base = t * kBTile; base < d_hi; base += 32) {
       const long long d = base + lane;
       bool distinct = false;
       int klo = 0, n = 0;
       if (d < d_hi) {
         unsigned v[8];
-        float s[8];
+        float sv[8];
         distinct = load_dual(J.duals, d, v);
         float mn = 3.4e38f, mx = -3.4e38f;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          s[e] = __ldg(J.scal + v[e]);
-          mn = fminf(mn, s[e]);
-          mx = fmaxf(mx, s[e]);
+          sv[e] = __ldg(J.scal + v[e]);
+          mn = fminf(mn, sv[e]);
+          mx = fmaxf(mx, sv[e]);
         }
         klo = batch_below(S, n_iso, mn);
         n = max(0, batch_below(S, n_iso, mx) - klo);
@@ -1961,27 +1973,29 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
           // each, relative to vertex 0's corner, which they differ from by
           // less than 2^16 per axis (every vertex cell holds a point within
           // one cell width of the dual's owner)
-          unsigned long long key[8];
-          int4 c0 = make_int4(0, 0, 0, 0);
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int4 cr = slot_cell_rt(J.bricks, v[e], J.logb);
-            if (e == 0) c0 = cr;
-            const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
-            W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
-                                       __fadd_rn(__int2float_rn(cr.z), h), s[e]);
-            W.s[e][lane] = s[e];
-            W.v[e][lane] = v[e];
-            key[e] = ((unsigned long long)(unsigned)(cr.z - c0.z + 65536) << 34) |
-                     ((unsigned long long)(unsigned)(cr.y - c0.y + 65536) << 17) | (unsigned)(cr.x - c0.x + 65536);
-          }
           // the hexahedron's 12 edges (a, b), a < b, in increasing order: the
-          // numbering the case table's edge ids use
+          // numbering the case table's edge ids use; an edge's bit is taken
+          // as soon as its upper vertex's key is known
           constexpr int kEa[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6};
           constexpr int kEb[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
+          unsigned long long key[8];
+          int c0x = 0, c0y = 0, c0z = 0;
           unsigned sw = 0;
 #pragma unroll
-          for (int k = 0; k < 12; ++k) sw |= (key[kEb[k]] < key[kEa[k]] ? 1u : 0u) << k;
+          for (int e = 0; e < 8; ++e) {
+            const int4 cr = J.logb == 3 ? slot_cell_tab<3>(J.bricks, cell_tab3, v[e])
+                                        : slot_cell_tab<2>(J.bricks, cell_tab2, v[e]);
+            if (e == 0) { c0x = cr.x; c0y = cr.y; c0z = cr.z; }
+            const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
+            W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
+                                       __fadd_rn(__int2float_rn(cr.z), h), sv[e]);
+            W.s[e][lane] = sv[e];
+            key[e] = ((unsigned long long)(unsigned)(cr.z - c0z + 65536) << 34) |
+                     ((unsigned long long)(unsigned)(cr.y - c0y + 65536) << 17) | (unsigned)(cr.x - c0x + 65536);
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+              if (kEb[k] == e) sw |= (key[e] < key[kEa[k]] ? 1u : 0u) << k;
+          }
           W.swap[lane] = sw;
         }
       }
@@ -1995,12 +2009,17 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
         const int src = pair_owner(excl, p);
         const int ks = __shfl_sync(kFull, klo, src) + (int)(p - __shfl_sync(kFull, excl, src));
         const bool live = p < n_pairs;
-        unsigned keep = 0, kk = 0;
+        unsigned keep = 0;
         int cas = 0;
         if (live) {
-          kk = S.idx[ks];
           cas = batch_case(&W.s[0][src], 32, S.v[ks]);
-          keep = batch_kept(((dmask >> src) & 1u) != 0, cas, &W.v[0][src], 32, sh, mc.edge_a, mc.edge_b);
+          if ((dmask >> src) & 1u) {
+            keep = (1u << sh.count[cas]) - 1u;
+          } else {   // a dual of fewer than 8 cells: its slots again (about 2 % of duals)
+            unsigned vv[8];
+            load_dual(J.duals, base + src, vv);
+            keep = kept_triangles(sh.packed[cas], sh.count[cas], vv, mc.edge_a, mc.edge_b);
+          }
         }
         const unsigned c = __popc(keep);
         const unsigned ci = warp_incl_scan(c, lane);
@@ -2008,25 +2027,24 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
         if (total == 0) continue;
         if (len + total > (unsigned)kBatchList) {   // list full: its vertices first
           __syncwarp();
-          batch_flush(lst, len, W, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
+          batch_flush(lst, len, W, E, tris, mc.edge_a, mc.edge_b);
           __syncwarp();
           len = 0;
         }
         if (c) {
-          unsigned row = atomicAdd(&tcnt[kk], c);   // rows inside the tile's run of segment kk
+          unsigned row = atomicAdd(&E.tcnt[ks], c);   // rows inside the tile's run of the segment
           unsigned pos = len + ci - c;
           const unsigned long long pk = sh.packed[cas];
           for (int tt = 0; tt < 5; ++tt)
             if ((keep >> tt) & 1u)
-              lst[pos++] = batch_entry(row++, (unsigned)src, kk, (unsigned)(pk >> (12 * tt)) & 0xFFFu);
+              lst[pos++] = batch_entry(row++, (unsigned)src, (unsigned)ks, (unsigned)(pk >> (12 * tt)) & 0xFFFu);
         }
         len += total;
       }
       __syncwarp();
-      batch_flush(lst, len, W, iso_sh, row0, rowend, tris, mc.edge_a, mc.edge_b);
+      batch_flush(lst, len, W, E, tris, mc.edge_a, mc.edge_b);
       __syncwarp();
     }
-    __syncthreads();
   }
 }
 
