@@ -1355,6 +1355,11 @@ constexpr int kMcSmemBytes = 4 * (kMcRowsWords + 8 * kTriStage + 8 * kTriStage *
 // triangles; the warp's 32 lanes take the step's 3T vertices in turn, stage
 // them, and write the step's triangles as one coalesced run. Optionally
 // writes per-dual case and triangle count instead.
+// A dual's tuple (32 bytes) on its way to L2 ahead of its load.
+__device__ __forceinline__ void prefetch_dual(const uint4* duals, long long d) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(duals + 2 * d));
+}
+
 // Edge key of a triangle vertex: the unordered pair of slots it interpolates
 // between (slots stay below 2^31), smaller first.
 __device__ __forceinline__ unsigned long long slot_pair(unsigned a, unsigned b) {
@@ -1386,6 +1391,11 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
   for (long long base = wid * 64; base < nd; base += nwarps * 64) {
     const long long d0 = base + lane, d1 = base + 32 + lane;
     const bool a0 = d0 < nd, a1 = d1 < nd;
+    {   // the warp's next step, fetched while this one runs
+      const long long n0 = d0 + nwarps * 64, n1 = d1 + nwarps * 64;
+      if (n0 < nd) prefetch_dual(duals, n0);
+      if (n1 < nd) prefetch_dual(duals, n1);
+    }
     unsigned v0[8], v1[8];
     float s0[8], s1[8];
     bool x0 = false, x1 = false;
@@ -1722,6 +1732,8 @@ __global__ void __launch_bounds__(256, 5) k_batch_count(const __grid_constant__ 
     __syncwarp();
     const long long d_hi = min(J.nd, (t + 1) * kBTile);
     for (long long base = t * kBTile; base < d_hi; base += kCountStep) {
+      if (base + kCountStep + lane < d_hi) prefetch_dual(J.duals, base + kCountStep + lane);
+      if (base + kCountStep + 32 + lane < d_hi) prefetch_dual(J.duals, base + kCountStep + 32 + lane);
       // duals lane and lane + 32 of the step: slots and scalars to shared
       // memory, the run of sorted iso-values crossing each
       int klo0 = 0, n0 = 0, klo1 = 0, n1 = 0;
@@ -1858,9 +1870,9 @@ __global__ void k_batch_bases(int n_q, const long long* totals, long long* off) 
 // of padding: lanes reading vertex e of dual i and vertex e' of dual i'
 // share a bank group only when e + i == e' + i' mod 8).
 struct BatchWarp {
-  float4 c[8][33];     // centre x, y, z and scalar (the fp32 operations of edge_vertex)
-  float s[8][32];      // the scalars again, for the case loop
-  unsigned swap[32];   // bit k: edge k's vertex b lies lower in (z, y, x) order
+  float4 c[8][33];              // centre x, y, z and scalar (the fp32 operations of edge_vertex)
+  float s[8][32];               // the scalars again, for the case loop
+  unsigned char ab[12][32];     // per edge its two vertices, the lower one in (z, y, x) order first
 };
 // A tile's iso-values and rows in k_batch_emit: tiles are handed to warps,
 // so that a warp never waits for the other warps of its CTA.
@@ -1874,13 +1886,12 @@ struct EmitTile {           // per iso-value, by position in S:
 // pairs adds at most 32 x 5).
 constexpr int kBatchList = 224;
 
-__device__ __forceinline__ float3 batch_vertex(const BatchWarp& W, int i, int k, unsigned long long ea,
-                                               unsigned long long eb, float iso) {
-  int a = (int)((ea >> (4 * k)) & 15), b = (int)((eb >> (4 * k)) & 15);
-  if ((W.swap[i] >> k) & 1u) {
-    const int t = a; a = b; b = t;
-  }
-  const float4 pa = W.c[a][i], pb = W.c[b][i];
+// Vertex on edge k of dual i at iso: from the cell with the lower corner,
+// t = (iso - sa) / (sb - sa), P = ca + t (cb - ca), every operation rounded
+// on its own (edge_vertex's order).
+__device__ __forceinline__ float3 batch_vertex(const BatchWarp& W, int i, int k, float iso) {
+  const unsigned ab = W.ab[k][i];
+  const float4 pa = W.c[ab & 15u][i], pb = W.c[ab >> 4][i];
   const float t = __fdiv_rn(__fsub_rn(iso, pa.w), __fsub_rn(pb.w, pa.w));
   return make_float3(__fadd_rn(pa.x, __fmul_rn(t, __fsub_rn(pb.x, pa.x))),
                      __fadd_rn(pa.y, __fmul_rn(t, __fsub_rn(pb.y, pa.y))),
@@ -1899,17 +1910,17 @@ __device__ __forceinline__ unsigned long long batch_entry(unsigned row, unsigned
 // The warp's listed triangles, one vertex per lane in turn: interpolated
 // from the dual's vertex data and written straight to its row (a run of
 // consecutive rows per segment, so consecutive lanes write consecutive
-// 12-byte vertices).
+// 12-byte vertices). fits: every row of the job lies below the capacity.
 __device__ __forceinline__ void batch_flush(const unsigned long long* lst, unsigned len, const BatchWarp& W,
-                                            const EmitTile& E, float* __restrict__ tris, unsigned long long ea,
-                                            unsigned long long eb) {
+                                            const EmitTile& E, float* __restrict__ tris, bool fits) {
   for (unsigned q = threadIdx.x & 31; q < 3u * len; q += 32) {
     const unsigned e = q / 3u, c = q - 3u * e;
     const unsigned long long ent = lst[e];
-    const unsigned k = (unsigned)(ent >> 37) & 63u;
+    const unsigned hi = (unsigned)(ent >> 32);   // lane, iso-value, edges
+    const unsigned k = (hi >> 5) & 63u;
     const long long row = E.row0[k] + (long long)(unsigned)ent;
-    if (row >= E.rowend[k]) continue;   // capacity: exact prefix only
-    const float3 p = batch_vertex(W, (int)((ent >> 32) & 31u), (int)((ent >> (43 + 4 * c)) & 15u), ea, eb, E.S.v[k]);
+    if (!fits && row >= E.rowend[k]) continue;   // capacity: exact prefix only
+    const float3 p = batch_vertex(W, (int)(hi & 31u), (int)((hi >> (11 + 4 * c)) & 15u), E.S.v[k]);
     float* out = tris + 9 * row + 3 * c;
     out[0] = p.x;
     out[1] = p.y;
@@ -1950,14 +1961,16 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
       E.rowend[ks] = min(__ldg(off + J.q0 + k + 1), total_cap);
     }
     __syncwarp();
+    const bool fits = __ldg(off + J.q0 + n_iso) <= total_cap;   // every row of the job fits
     const long long d_hi = min(J.nd, (t + 1) * kBTile);
     for (long long base = t * kBTile; base < d_hi; base += 32) {
       const long long d = base + lane;
+      if (d + 32 < d_hi) prefetch_dual(J.duals, d + 32);
       bool distinct = false;
       int klo = 0, n = 0;
+      unsigned v[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // (slot 0 stands in past the tile's end)
+      float sv[8];
       if (d < d_hi) {
-        unsigned v[8];
-        float sv[8];
         distinct = load_dual(J.duals, d, v);
         float mn = 3.4e38f, mx = -3.4e38f;
 #pragma unroll
@@ -1968,36 +1981,52 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
         }
         klo = batch_below(S, n_iso, mn);
         n = max(0, batch_below(S, n_iso, mx) - klo);
-        if (n > 0) {   // some iso-value crosses it: its vertex data, once for all of them
-          // (z, y, x) order of the vertex cells' corners as one 64-bit key
-          // each, relative to vertex 0's corner, which they differ from by
-          // less than 2^16 per axis (every vertex cell holds a point within
-          // one cell width of the dual's owner)
-          // the hexahedron's 12 edges (a, b), a < b, in increasing order: the
-          // numbering the case table's edge ids use; an edge's bit is taken
-          // as soon as its upper vertex's key is known
-          constexpr int kEa[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6};
-          constexpr int kEb[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
+      }
+      if (__any_sync(kFull, n > 0)) {   // vertex data of the warp's crossing duals, once for all values
+        // the hexahedron's 12 edges (a, b), a < b, in increasing order: the
+        // numbering the case table's edge ids use
+        constexpr int kEa[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6};
+        constexpr int kEb[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
+        int lmin = 64, lmax = -1;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int4 cr = J.logb == 3 ? slot_cell_tab<3>(J.bricks, cell_tab3, v[e])
+                                      : slot_cell_tab<2>(J.bricks, cell_tab2, v[e]);
+          lmin = min(lmin, cr.w);
+          lmax = max(lmax, cr.w);
+          const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
+          W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
+                                     __fadd_rn(__int2float_rn(cr.z), h), sv[e]);
+          W.s[e][lane] = sv[e];
+          if (e == 3) __syncwarp();   // at most four cells' loads in flight per lane: fewer live registers
+        }
+        // edge k's bit: its vertex b's cell lies lower in (z, y, x) order.
+        // With all 8 cells on one level the cells sit one width apart along
+        // each edge's axis, so no bit is set; otherwise compare the corners,
+        // as one 64-bit key each relative to vertex 0's corner (they differ
+        // by less than 2^16 per axis: every vertex cell holds a point within
+        // one cell width of the dual's owner), an edge's bit taken as soon
+        // as its upper vertex's key is known
+        unsigned sw = 0;
+        if (__any_sync(kFull, lmin != lmax)) {
           unsigned long long key[8];
           int c0x = 0, c0y = 0, c0z = 0;
-          unsigned sw = 0;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int4 cr = J.logb == 3 ? slot_cell_tab<3>(J.bricks, cell_tab3, v[e])
                                         : slot_cell_tab<2>(J.bricks, cell_tab2, v[e]);
             if (e == 0) { c0x = cr.x; c0y = cr.y; c0z = cr.z; }
-            const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
-            W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
-                                       __fadd_rn(__int2float_rn(cr.z), h), sv[e]);
-            W.s[e][lane] = sv[e];
             key[e] = ((unsigned long long)(unsigned)(cr.z - c0z + 65536) << 34) |
                      ((unsigned long long)(unsigned)(cr.y - c0y + 65536) << 17) | (unsigned)(cr.x - c0x + 65536);
 #pragma unroll
             for (int k = 0; k < 12; ++k)
               if (kEb[k] == e) sw |= (key[e] < key[kEa[k]] ? 1u : 0u) << k;
+            if (e == 3) __syncwarp();
           }
-          W.swap[lane] = sw;
         }
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          W.ab[k][lane] = (unsigned char)(((sw >> k) & 1u) ? (kEb[k] | (kEa[k] << 4)) : (kEa[k] | (kEb[k] << 4)));
       }
       const unsigned dmask = __ballot_sync(kFull, distinct);
       const unsigned incl = warp_incl_scan((unsigned)n, lane), excl = incl - (unsigned)n;
@@ -2027,7 +2056,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
         if (total == 0) continue;
         if (len + total > (unsigned)kBatchList) {   // list full: its vertices first
           __syncwarp();
-          batch_flush(lst, len, W, E, tris, mc.edge_a, mc.edge_b);
+          batch_flush(lst, len, W, E, tris, fits);
           __syncwarp();
           len = 0;
         }
@@ -2042,7 +2071,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
         len += total;
       }
       __syncwarp();
-      batch_flush(lst, len, W, E, tris, mc.edge_a, mc.edge_b);
+      batch_flush(lst, len, W, E, tris, fits);
       __syncwarp();
     }
   }

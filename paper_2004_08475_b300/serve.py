@@ -91,8 +91,10 @@ class Server:
         self.workers = []
         self.stats = collections.Counter()
         self._rid = 0
-        # captured batch graphs per worker: key (data sets, iso counts, buffers) -> graph
+        # captured batch graphs per worker: key (data sets, iso counts, buffers) -> graph;
+        # a combination is captured the second time it comes (seen: keys met once)
         self.graphs: dict[int, "collections.OrderedDict"] = collections.defaultdict(collections.OrderedDict)
+        self.seen: dict[int, "collections.OrderedDict"] = collections.defaultdict(collections.OrderedDict)
         # Graph capture must not overlap device allocation or release in other
         # threads (context creation, locator buffers, eviction, buffer growth);
         # kernel work and graph replays run outside this lock.
@@ -369,12 +371,19 @@ class Server:
             self.stats["graph_replays"] += 1
         else:
             launch()
-            if self.use_graphs:
+            seen = self.seen[w]
+            if self.use_graphs and key in seen:   # recurring: capture it for the next time
                 g = self._capture(launch, stream)
                 with self.cv:
                     graphs[key] = g
                     while len(graphs) > MAX_GRAPHS:
                         graphs.popitem(last=False)
+                    seen.pop(key, None)
+                self.stats["graph_captures"] += 1
+            elif self.use_graphs:
+                seen[key] = True
+                while len(seen) > 4 * MAX_GRAPHS:
+                    seen.popitem(last=False)
         bufs["h_offs"][:nq + 1].copy_(d_offs, non_blocking=True)
         stream.synchronize()
         offs = bufs["h_offs"][:nq + 1].tolist()
@@ -402,12 +411,18 @@ class Server:
                 r.tris = [out[offs[j + i]:offs[j + i + 1]].cpu() for i in range(len(r.isos))]
 
     def _capture(self, launch, stream):
-        """CUDA graph of the batched step (counts, prefix sums, emission)."""
-        stream.synchronize()
+        """CUDA graph of the batched step (counts, prefix sums, emission),
+        captured on the worker's own stream. (torch.cuda.graph's context
+        manager would also synchronise the whole device, run the garbage
+        collector and empty the allocator's cache on every capture, stalling
+        the other workers' batches.)"""
         g = torch.cuda.CUDAGraph()
-        with self.cuda_lock:
-            with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+        with self.cuda_lock, torch.cuda.stream(stream):
+            g.capture_begin(capture_error_mode="thread_local")
+            try:
                 launch()
+            finally:
+                g.capture_end()
         return g
 
 

@@ -145,11 +145,12 @@ def test_mix_equals_alone():
     for r in reqs:
         assert r.done.wait(120)
     # the large octree alone exceeds the budget, so in the burst any data set
-    # may be evicted before it is served again; four identical requests one
+    # may be evicted before it is served again; ten identical requests one
     # after another keep the sphere resident, and with three worker slots one
-    # of them serves it twice and replays its graph
+    # of them serves it at least four times: a combination is captured the
+    # second time a worker meets it and replayed from the third
     iso_sphere = float(np.quantile(data["sphere"][2].numpy(), 0.5))
-    for _ in range(4):
+    for _ in range(10):
         r = srv.submit("sphere", [iso_sphere])
         assert r.done.wait(120)
         reqs.append(r)
