@@ -1420,8 +1420,18 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
     if (EMIT) {
       if (__ballot_sync(kFull, (k0 | k1) != 0) == 0) continue;
       const unsigned mine = __popc(k0) + __popc(k1);
-      const unsigned total = __reduce_add_sync(kFull, mine);
-      long long idx = warp_append(mine, counter);
+      // the warp's run of output rows: one atomic per warp, whose result is
+      // read only where the rows are written, so that its round trip
+      // overlaps the vertex work
+      unsigned incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned total = __shfl_sync(kFull, incl, 31), excl = incl - mine;
+      unsigned long long wbase = 0;
+      if (lane == 31) wbase = atomicAdd(counter, (unsigned long long)total);
       unsigned* r0 = rows_v + lane * kRow;   // rows lane and 32 + lane: conflict-free
       if (k0) {
 #pragma unroll
@@ -1432,8 +1442,7 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
         for (int e = 0; e < 8; ++e) r0[32 * kRow + e] = v1[e];
       }
       if (total <= (unsigned)kTriStage) {
-        const long long first = __shfl_sync(kFull, idx, 0);
-        unsigned pos = (unsigned)(idx - first);
+        unsigned pos = excl;
         const unsigned long long p0 = sh.packed[c0], p1 = sh.packed[c1];
         for (int t = 0; t < 5; ++t)
           if ((k0 >> t) & 1u) list[pos++] = (unsigned)lane | ((unsigned)(p0 >> (12 * t)) & 0xFFFu) << 8;
@@ -1458,6 +1467,7 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
           }
         }
         __syncwarp();
+        const long long first = (long long)__shfl_sync(kFull, wbase, 31);
         if (KEYS) {
           const long long lim = min((long long)total, cap - first) * 3;
           unsigned long long* out = reinterpret_cast<unsigned long long*>(tris) + 3 * first;
@@ -1470,6 +1480,7 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
         }
         __syncwarp();
       } else if (KEYS) {   // more triangles than the stage holds: each lane writes its own keys
+        long long idx = (long long)__shfl_sync(kFull, wbase, 31) + excl;
         unsigned long long* out = reinterpret_cast<unsigned long long*>(tris);
         const unsigned long long kp[2] = {sh.packed[c0], sh.packed[c1]};
         const unsigned km[2] = {k0, k1};
@@ -1490,6 +1501,7 @@ __global__ void __launch_bounds__(256, 4) k_mc(Locator L, const uint4* __restric
         }
         __syncwarp();
       } else {   // more triangles than the stage holds: each lane writes its own (scalars in the stage)
+        long long idx = (long long)__shfl_sync(kFull, wbase, 31) + excl;
         float* q0 = wst + lane * 2 * kRow;
         if (k0) {
 #pragma unroll
