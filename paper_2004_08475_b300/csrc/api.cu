@@ -574,7 +574,7 @@ int dual_cells_owned(amr_ctx* c, int x0, int x1, int64_t* n_dual) {
     const long long nd = (long long)c->host_sc->n_dual;
     if (nd <= c->dual_cap) {
       c->n_dual = nd;
-      AMR_TRY(ensure(c->bwork, batch_workspace_bytes((nd + kBTile - 1) / kBTile * kMaxIso)));
+      AMR_TRY(ensure(c->bwork, batch_workspace_bytes((nd + batch_tile(nd) - 1) / batch_tile(nd) * kMaxIso)));
       c->stage = 3;
       *n_dual = nd;
       return AMR_OK;
@@ -622,7 +622,7 @@ int amr_dual_cells_iso(amr_ctx* c, float iso, float* tris, int64_t cap, int64_t*
     }
     const long long nt = (long long)c->host_sc->n_tri[0];
     c->n_dual = nd;
-    AMR_TRY(ensure(c->bwork, batch_workspace_bytes((nd + kBTile - 1) / kBTile * kMaxIso)));
+    AMR_TRY(ensure(c->bwork, batch_workspace_bytes((nd + batch_tile(nd) - 1) / batch_tile(nd) * kMaxIso)));
     c->stage = 3;
     *n_dual = nd;
     *n_tris = nt;

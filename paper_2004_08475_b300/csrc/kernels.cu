@@ -1614,7 +1614,7 @@ __global__ void __launch_bounds__(256) k_weld_index(const unsigned long long* __
 }
 
 // Batched iso-values over one or several resident dual lists (one launch per
-// pass for all of them). The dual lists are cut into tiles of kBTile duals;
+// pass for all of them). Each dual list is cut into tiles (batch_tile duals);
 // a job is one data set's dual list with its run of iso-values, and every
 // (job, iso-value) pair owns one output segment. Three passes:
 //   k_batch_count: per tile, the kept triangles of every iso-value of its
@@ -1742,8 +1742,8 @@ __global__ void __launch_bounds__(256, 5) k_batch_count(const __grid_constant__ 
     for (int k = lane; k < n_iso; k += 32) C.cnt[k] = 0;
     batch_sort_isos(isos + J.q0, n_iso, C.S);
     __syncwarp();
-    const long long d_hi = min(J.nd, (t + 1) * kBTile);
-    for (long long base = t * kBTile; base < d_hi; base += kCountStep) {
+    const long long d_hi = min(J.nd, (t + 1) * J.tile);
+    for (long long base = t * J.tile; base < d_hi; base += kCountStep) {
       if (base + kCountStep + lane < d_hi) prefetch_dual(J.duals, base + kCountStep + lane);
       if (base + kCountStep + 32 + lane < d_hi) prefetch_dual(J.duals, base + kCountStep + 32 + lane);
       // duals lane and lane + 32 of the step: slots and scalars to shared
@@ -1974,8 +1974,8 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
     }
     __syncwarp();
     const bool fits = __ldg(off + J.q0 + n_iso) <= total_cap;   // every row of the job fits
-    const long long d_hi = min(J.nd, (t + 1) * kBTile);
-    for (long long base = t * kBTile; base < d_hi; base += 32) {
+    const long long d_hi = min(J.nd, (t + 1) * J.tile);
+    for (long long base = t * J.tile; base < d_hi; base += 32) {
       const long long d = base + lane;
       if (d + 32 < d_hi) prefetch_dual(J.duals, d + 32);
       bool distinct = false;
@@ -2318,6 +2318,12 @@ cudaError_t launch_weld_index(const unsigned long long* tkeys, long long n_tri, 
   return cudaGetLastError();
 }
 
+int batch_tile(long long nd) {
+  int t = kBTile;
+  while (t > 256 && nd < 16384ll * t) t >>= 1;
+  return t;
+}
+
 void batch_add_job(BatchTable& T, const uint4* duals, const float* scal, const int4* bricks, long long nd, int logb,
                    int n_iso) {
   BatchJob& J = T.job[T.n_jobs];
@@ -2327,7 +2333,8 @@ void batch_add_job(BatchTable& T, const uint4* duals, const float* scal, const i
   J.nd = nd;
   J.logb = logb;
   J.tile0 = T.n_tiles;
-  J.tiles = (nd + kBTile - 1) / kBTile;
+  J.tile = batch_tile(nd);
+  J.tiles = (nd + J.tile - 1) / J.tile;
   J.cbase = T.n_counters;
   J.q0 = T.n_q;
   J.n_iso = n_iso;

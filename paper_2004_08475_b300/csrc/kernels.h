@@ -147,7 +147,11 @@ cudaError_t launch_weld_index(const unsigned long long* tkeys, long long n_tri, 
 // kernels.cu): a job is one data set's dual list with its run of n_iso
 // iso-values; job j's iso-values are entries q0 .. q0 + n_iso - 1 of the
 // batch's iso array, and (job, value) q owns output segment q.
-constexpr int kBTile = 4096;   // duals per tile
+constexpr int kBTile = 4096;   // most duals per tile
+// Tile of a job's dual list in the batched passes: the largest power of two
+// up to kBTile (at least 256) that still cuts the list into about 16384
+// tiles, so that a small data set's tiles still occupy every warp.
+int batch_tile(long long nd);
 constexpr int kMaxJobs = 32;   // data sets in one batch
 
 struct BatchJob {
@@ -158,6 +162,7 @@ struct BatchJob {
   long long tile0;   // first tile of this job in the batch's tile numbering
   long long tiles;   // tiles of this job
   long long cbase;   // first counter of this job: counters [n_iso][tiles]
+  long long tile;    // duals per tile (batch_tile(nd))
   int logb;
   int q0;            // first segment (index into the batch's iso-values)
   int n_iso;
