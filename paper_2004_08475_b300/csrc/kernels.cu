@@ -2000,41 +2000,58 @@ __global__ void __launch_bounds__(256, 3) k_batch_emit(const __grid_constant__ B
         // numbering the case table's edge ids use
         constexpr int kEa[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6};
         constexpr int kEb[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
-        int lmin = 64, lmax = -1;
+        unsigned sw = 0;   // bit k: edge k's vertex b's cell lies lower in (z, y, x) order
+        if (__all_sync(kFull, distinct || n == 0)) {
+          // every crossing dual of the step is 8 cells of one level: they sit
+          // one width apart along each axis from vertex 0's, and no edge
+          // is reversed
+          const int4 c0 = J.logb == 3 ? slot_cell_tab<3>(J.bricks, cell_tab3, v[0])
+                                      : slot_cell_tab<2>(J.bricks, cell_tab2, v[0]);
+          const float h = __fmul_rn(__int2float_rn(1 << c0.w), 0.5f);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int4 cr = J.logb == 3 ? slot_cell_tab<3>(J.bricks, cell_tab3, v[e])
-                                      : slot_cell_tab<2>(J.bricks, cell_tab2, v[e]);
-          lmin = min(lmin, cr.w);
-          lmax = max(lmax, cr.w);
-          const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
-          W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
-                                     __fadd_rn(__int2float_rn(cr.z), h), sv[e]);
-          W.s[e][lane] = sv[e];
-          if (e == 3) __syncwarp();   // at most four cells' loads in flight per lane: fewer live registers
-        }
-        // edge k's bit: its vertex b's cell lies lower in (z, y, x) order.
-        // With all 8 cells on one level the cells sit one width apart along
-        // each edge's axis, so no bit is set; otherwise compare the corners,
-        // as one 64-bit key each relative to vertex 0's corner (they differ
-        // by less than 2^16 per axis: every vertex cell holds a point within
-        // one cell width of the dual's owner), an edge's bit taken as soon
-        // as its upper vertex's key is known
-        unsigned sw = 0;
-        if (__any_sync(kFull, lmin != lmax)) {
-          unsigned long long key[8];
-          int c0x = 0, c0y = 0, c0z = 0;
+          for (int e = 0; e < 8; ++e) {
+            const int x = c0.x + ((e & 1) << c0.w), y = c0.y + (((e >> 1) & 1) << c0.w),
+                      z = c0.z + ((e >> 2) << c0.w);
+            W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(x), h), __fadd_rn(__int2float_rn(y), h),
+                                       __fadd_rn(__int2float_rn(z), h), sv[e]);
+            W.s[e][lane] = sv[e];
+          }
+        } else {
+          int lmin = 64, lmax = -1;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int4 cr = J.logb == 3 ? slot_cell_tab<3>(J.bricks, cell_tab3, v[e])
                                         : slot_cell_tab<2>(J.bricks, cell_tab2, v[e]);
-            if (e == 0) { c0x = cr.x; c0y = cr.y; c0z = cr.z; }
-            key[e] = ((unsigned long long)(unsigned)(cr.z - c0z + 65536) << 34) |
-                     ((unsigned long long)(unsigned)(cr.y - c0y + 65536) << 17) | (unsigned)(cr.x - c0x + 65536);
+            lmin = min(lmin, cr.w);
+            lmax = max(lmax, cr.w);
+            const float h = __fmul_rn(__int2float_rn(1 << cr.w), 0.5f);
+            W.c[e][lane] = make_float4(__fadd_rn(__int2float_rn(cr.x), h), __fadd_rn(__int2float_rn(cr.y), h),
+                                       __fadd_rn(__int2float_rn(cr.z), h), sv[e]);
+            W.s[e][lane] = sv[e];
+            if (e == 3) __syncwarp();   // at most four cells' loads in flight per lane: fewer live registers
+          }
+          // edge k's bit: its vertex b's cell lies lower in (z, y, x) order.
+          // With all 8 cells on one level the cells sit one width apart along
+          // each edge's axis, so no bit is set; otherwise compare the corners,
+          // as one 64-bit key each relative to vertex 0's corner (they differ
+          // by less than 2^16 per axis: every vertex cell holds a point within
+          // one cell width of the dual's owner), an edge's bit taken as soon
+          // as its upper vertex's key is known
+          if (__any_sync(kFull, lmin != lmax)) {
+            unsigned long long key[8];
+            int c0x = 0, c0y = 0, c0z = 0;
 #pragma unroll
-            for (int k = 0; k < 12; ++k)
-              if (kEb[k] == e) sw |= (key[e] < key[kEa[k]] ? 1u : 0u) << k;
-            if (e == 3) __syncwarp();
+            for (int e = 0; e < 8; ++e) {
+              const int4 cr = J.logb == 3 ? slot_cell_tab<3>(J.bricks, cell_tab3, v[e])
+                                          : slot_cell_tab<2>(J.bricks, cell_tab2, v[e]);
+              if (e == 0) { c0x = cr.x; c0y = cr.y; c0z = cr.z; }
+              key[e] = ((unsigned long long)(unsigned)(cr.z - c0z + 65536) << 34) |
+                       ((unsigned long long)(unsigned)(cr.y - c0y + 65536) << 17) | (unsigned)(cr.x - c0x + 65536);
+#pragma unroll
+              for (int k = 0; k < 12; ++k)
+                if (kEb[k] == e) sw |= (key[e] < key[kEa[k]] ? 1u : 0u) << k;
+              if (e == 3) __syncwarp();
+            }
           }
         }
 #pragma unroll
