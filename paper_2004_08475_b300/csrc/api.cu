@@ -71,6 +71,10 @@ McConst make_mc_const() {
 struct amr_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  // the locator build's second stream: neighbours and brick order (they
+  // need only the brick table) run beside the placement of the cells
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sm_count = 148;
   // input (borrowed or owned)
   long long n = 0;
@@ -162,17 +166,18 @@ cudaEvent_t take_event(amr_ctx* c) {
 struct KernelTimer {
   amr_ctx* c;
   int k;
+  cudaStream_t st;
   cudaEvent_t a = nullptr, b = nullptr;
-  KernelTimer(amr_ctx* c_, int k_) : c(c_), k(k_) {
+  KernelTimer(amr_ctx* c_, int k_, cudaStream_t st_ = nullptr) : c(c_), k(k_), st(st_ ? st_ : c_->stream) {
     if (c->timing) {
       a = take_event(c);
       b = take_event(c);
-      cudaEventRecord(a, c->stream);
+      cudaEventRecord(a, st);
     }
   }
   ~KernelTimer() {
     if (c->timing) {
-      cudaEventRecord(b, c->stream);
+      cudaEventRecord(b, st);
       c->pending[k].push_back({a, b});
       c->launches[k]++;
     }
@@ -180,6 +185,15 @@ struct KernelTimer {
 };
 
 Scratch* dev_sc(amr_ctx* c) { return static_cast<Scratch*>(c->scratch.p); }
+
+// The context's second stream and its fork/join events, made on first use
+// (on the context's device, current here).
+int side_stream(amr_ctx* c) {
+  if (!c->side) AMR_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  if (!c->ev_fork) AMR_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  if (!c->ev_join) AMR_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  return AMR_OK;
+}
 
 // Resets the device scratch counters (stream-ordered).
 int reset_scratch(amr_ctx* c) {
@@ -325,6 +339,9 @@ void amr_destroy(amr_ctx* c) {
       cudaEventDestroy(p.second);
     }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -464,6 +481,38 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
   AMR_TRY(ensure(c->view, (size_t)c->n_slots * 4));
   const bool binned_ok = binned && codes != nullptr;
   if (c->n_slots) {
+    // neighbours and the brick order need only the brick table and the
+    // bricks: they run on the side stream while the cells are placed
+    AMR_TRY(ensure(c->nbr, (size_t)c->n_bricks * 27 * 4));
+    AMR_TRY(ensure(c->border, (size_t)c->n_bricks * 4));
+    AMR_TRY(ensure(c->bcount, (size_t)kOrderBuckets * 4));
+    AMR_TRY(side_stream(c));
+    AMR_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    AMR_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    const Locator Lt = make_locator(c);
+    {
+      KernelTimer kt(c, KT_NEIGHBORS, c->side);
+      AMR_CUDA(launch_brick_neighbors(logb, Lt, c->n_bricks, static_cast<int*>(c->nbr.p),
+                                      grid_for(c, c->n_bricks * 27, 256, 8), c->side));
+    }
+    // the dual pass visits the bricks bucket by bucket along a Morton curve
+    unsigned* cnt = static_cast<unsigned*>(c->bcount.p);
+    AMR_CUDA(cudaMemsetAsync(cnt, 0, (size_t)kOrderBuckets * 4, c->side));
+    {
+      KernelTimer kt(c, KT_ORDER_COUNT, c->side);
+      AMR_CUDA(launch_brick_order_count(Lt.bricks, c->n_bricks, frame, cnt, grid_for(c, c->n_bricks, 256, 8),
+                                        c->side));
+    }
+    {
+      KernelTimer kt(c, KT_ORDER_SCAN, c->side);
+      AMR_CUDA(launch_brick_order_scan(cnt, c->side));
+    }
+    {
+      KernelTimer kt(c, KT_ORDER_SCATTER, c->side);
+      AMR_CUDA(launch_brick_order_scatter(Lt.bricks, c->n_bricks, frame, cnt, static_cast<int*>(c->border.p),
+                                          grid_for(c, c->n_bricks, 256, 8), c->side));
+    }
+    AMR_CUDA(cudaEventRecord(c->ev_join, c->side));
     // binned placement unless asked otherwise or the input is small; it
     // needs the insert pass's cell codes, so a table too large for them
     // (after rebuilds) falls back to the direct scatter
@@ -505,31 +554,7 @@ int amr_build_locator(amr_ctx* c, const amr_locator_opts* opts) {
                                     c->n_slots, overlap, dev_sc(c), grid_for(c, c->n_slots, block, 2048 / block),
                                     block, c->stream));
     }
-    AMR_TRY(ensure(c->nbr, (size_t)c->n_bricks * 27 * 4));
-    {
-      KernelTimer kt(c, KT_NEIGHBORS);
-      AMR_CUDA(launch_brick_neighbors(logb, L, c->n_bricks, static_cast<int*>(c->nbr.p),
-                                      grid_for(c, c->n_bricks * 27, 256, 8), c->stream));
-    }
-    // the dual pass visits the bricks bucket by bucket along a Morton curve
-    AMR_TRY(ensure(c->border, (size_t)c->n_bricks * 4));
-    AMR_TRY(ensure(c->bcount, (size_t)kOrderBuckets * 4));
-    unsigned* cnt = static_cast<unsigned*>(c->bcount.p);
-    AMR_CUDA(cudaMemsetAsync(cnt, 0, (size_t)kOrderBuckets * 4, c->stream));
-    {
-      KernelTimer kt(c, KT_ORDER_COUNT);
-      AMR_CUDA(launch_brick_order_count(L.bricks, c->n_bricks, frame, cnt, grid_for(c, c->n_bricks, 256, 8),
-                                        c->stream));
-    }
-    {
-      KernelTimer kt(c, KT_ORDER_SCAN);
-      AMR_CUDA(launch_brick_order_scan(cnt, c->stream));
-    }
-    {
-      KernelTimer kt(c, KT_ORDER_SCATTER);
-      AMR_CUDA(launch_brick_order_scatter(L.bricks, c->n_bricks, frame, cnt, static_cast<int*>(c->border.p),
-                                          grid_for(c, c->n_bricks, 256, 8), c->stream));
-    }
+    AMR_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     AMR_TRY(read_scratch(c));
     const int rc = err_code(c->host_sc->err);
     if (rc != AMR_OK) return rc;
