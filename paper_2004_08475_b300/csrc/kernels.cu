@@ -1770,10 +1770,10 @@ __global__ void __launch_bounds__(256, 5) k_batch_count(const __grid_constant__ 
           }
           klo = batch_below(S, n_iso, mn);
           n = max(0, batch_below(S, n_iso, mx) - klo);
-          if (n > 0) {
+          if (n > 0) {   // (the slots matter only for a dual of fewer than 8 cells)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-              wv[w][e][i] = v[e];
+              if (!distinct) wv[w][e][i] = v[e];
               wsc[w][e][i] = sv[e];
             }
           }
