@@ -353,11 +353,11 @@ const char* amr_kernel_name(int k);
  * Errors as amr_build_locator / amr_iso, plus AMR_ERR_RANGE when n exceeds
  * the limit, when the cells fill their 4^3 bricks to less than 1/8 on
  * average, or when more than 2 * AMR_NOALLOC_MAX_CELLS dual cells result.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. All calls share the array and each call resets what it uses, so
- * calls that overlap on the GPU (other host threads or streams) race.
- * Synchronises the stream. */
+ * The call synchronises the stream (it reads the counts back), so it cannot
+ * be captured in a CUDA graph. The first call on a device also looks up the
+ * array's device address (once per device, with that device current). All
+ * calls share the array and each call resets what it uses, so calls that
+ * overlap on the GPU (other host threads or streams) race. */
 #define AMR_NOALLOC_MAX_CELLS 65536
 #define AMR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int amr_extract_noalloc(const int32_t* xyz, const uint8_t* level,
